@@ -1,0 +1,220 @@
+/*
+ * mih.h -- exact k-nearest-neighbour and r-neighbour search in Hamming space
+ * by multi-index hashing (MIH) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: M. Norouzi, A. Punjani, D. J. Fleet, "Fast Exact Search in Hamming
+ * Space with Multi-Index Hashing" (arXiv:1307.2982).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Codes.   A database or query code of q bits (q in {64, 128, 256}) is stored
+ *          as W = q/64 consecutive uint64 words, row-major: code i occupies
+ *          words [i*W, (i+1)*W).  Bit b of a code is bit (b % 64) of word
+ *          (b / 64).  Ids are the row numbers 0..n-1 as uint32 (n < 2^32 - 1;
+ *          4-byte ids as in Sec. 6 "Memory Requirements").
+ * Order.   Results are ordered by (Hamming distance, id) ascending.  The paper
+ *          allows any choice among equidistant codes (Sec. 5.2); the id
+ *          tie-break makes every answer unique and schedule-independent.
+ * Memory.  Unless a parameter says "host", a pointer is a CUDA device pointer
+ *          on the current device.  The library never takes ownership of a
+ *          caller pointer; outputs are written into caller-allocated buffers.
+ *          Scratch memory comes from a stream-ordered pool owned by the
+ *          library (cudaMallocAsync on a private pool of the current device).
+ * Streams. `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *          default stream).  Work is enqueued on it; entry points that must
+ *          read sizes back (build, knn, rnear) synchronise that stream before
+ *          returning.  Inputs must stay unchanged until the call returns.
+ * Errors.  Every entry point returns a status; no exception, abort or device
+ *          trap crosses the boundary.  mih_last_error() gives a detail string
+ *          for the calling host thread.  After MIH_ECUDA the CUDA context
+ *          may be unusable (e.g. a caller pointer that is not device memory).
+ */
+#ifndef MIH_H_
+#define MIH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MIH_API __attribute__((visibility("default")))
+#else
+#define MIH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MIH_OK = 0,
+    MIH_EINVAL = 1,      /* invalid argument (size, q, m, k, r, null pointer) */
+    MIH_ENOMEM = 2,      /* device scratch or index allocation failed */
+    MIH_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    MIH_EOVERFLOW = 4,   /* mih_rnear: results exceed `capacity` (sizes returned) */
+    MIH_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    MIH_EINTERNAL = 6    /* an internal consistency check failed */
+} mih_status;
+
+/* Opaque index: m substring hash tables over a borrowed code array. */
+typedef struct mih_index mih_index;
+
+/* Table representation per substring (Sec. 6 "Implementation details"). */
+enum {
+    MIH_TABLE_AUTO = 0,    /* direct for s <= 24 bits, sparse above */
+    MIH_TABLE_DIRECT = 1,  /* CSR over all 2^s buckets: offsets[2^s + 1] */
+    MIH_TABLE_SPARSE = 2   /* sorted non-empty keys + open-addressing index */
+};
+
+typedef struct {
+    int32_t table_kind;    /* MIH_TABLE_*; DIRECT requires s <= 28 */
+    int32_t reserved[15];  /* must be zero */
+} mih_params;
+
+/* Aggregate work counters of one mih_knn / mih_rnear call (host struct). */
+typedef struct {
+    uint64_t lookups;            /* buckets examined (Sec. 3, "lookups") */
+    uint64_t candidates_raw;     /* bucket entries read */
+    uint64_t candidates_unique;  /* candidates left after duplicate removal */
+    uint64_t steps;              /* Alg. 3 steps executed, summed over queries */
+    uint64_t phase2_queries;     /* k-NN queries re-collected in a second pass */
+    uint64_t waves;              /* search waves launched */
+} mih_stats;
+
+typedef struct {
+    int32_t q, m, W;
+    int32_t substring_offset[256];  /* first code bit of substring j */
+    int32_t substring_length[256];  /* s_j */
+    int32_t table_kind[256];        /* MIH_TABLE_DIRECT or MIH_TABLE_SPARSE */
+    uint64_t n;
+    uint64_t distinct_keys[256];    /* non-empty buckets of table j */
+    uint64_t max_bucket[256];       /* largest bucket of table j */
+    uint64_t index_bytes;           /* device bytes owned by the index */
+} mih_index_info;
+
+/* ------------------------------------------------------------------------
+ * mih_build -- Algorithm 1 (Sec. 2.2): build one hash table per substring.
+ *
+ * codes   device, uint64[n][q/64], borrowed: the index keeps this pointer
+ *         and reads it during every search; the caller keeps the memory
+ *         alive and unchanged until mih_free.
+ * n       number of codes, 0 <= n < 2^32 - 1.
+ * q       code length in bits: 64, 128 or 256.
+ * m       number of substrings, 1 <= m <= q, with every substring at most 32
+ *         bits (m >= q/32).  Substring j covers contiguous bits; the first
+ *         m - (q mod m) substrings have floor(q/m) bits and the rest
+ *         ceil(q/m) bits (Sec. 2.1 footnote).
+ * params  host, nullable (NULL = defaults).
+ * out     host; receives the index on MIH_OK, NULL otherwise.
+ * Each table is a stable radix sort of (substring key, id), written as CSR
+ * buckets: direct-addressed offsets for short substrings, sorted distinct
+ * keys plus an open-addressing key index for long ones.  Synchronises
+ * `stream`.
+ * Errors: MIH_EINVAL (q, m, n, pointers), MIH_ENOMEM, MIH_ECUDA.
+ */
+MIH_API mih_status mih_build(const uint64_t *codes, uint64_t n, int q, int m,
+                     const mih_params *params, void *stream, mih_index **out);
+
+/* Release an index and the device memory it owns (not the codes).  NULL ok. */
+MIH_API void mih_free(mih_index *index);
+
+/* Fill `info` (host) with the index layout and sizes. */
+MIH_API mih_status mih_index_get_info(const mih_index *index, mih_index_info *info);
+
+/* ------------------------------------------------------------------------
+ * mih_knn -- Algorithm 3 (Sec. 4): exact k-NN of each query by multi-index
+ * hashing with a growing search radius.
+ *
+ * queries      device, uint64[nq][q/64].
+ * nq           number of queries, 0 <= nq <= 2^23.
+ * k            device uint32[nq] per-query k, or NULL to use k_uniform.
+ * k_uniform    k for every query when `k` is NULL.
+ * out_offsets  device uint64[nq+1] CSR offsets of each query's results when
+ *              `k` is given (out_offsets[i+1] - out_offsets[i] = k[i]); NULL
+ *              when k is uniform (query i then writes at i * k_uniform).
+ * out_ids      device uint32, per query min(k, n) ids in (distance, id)
+ *              order, then 0xFFFFFFFF padding up to k.
+ * out_dist     device int32, the matching distances, -1 for padding.
+ * query_stats  device uint64[nq][4] or NULL: per query lookups, raw
+ *              candidates, unique candidates, last step executed.  In the
+ *              paper's stopping rule the last step equals the k-th distance.
+ * stats        host, nullable: aggregate counters of this call.
+ * Every k must satisfy 1 <= k <= MIH_MAX_K.  Synchronises `stream`.
+ * Step t searches ring floor(t/m) of table (t mod m); a query stops after
+ * the first step t at which at least min(k, n) codes within t bits were
+ * found (Alg. 3; all codes within t bits are found by then, Prop. 2).
+ * Errors: MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EINTERNAL.
+ */
+#define MIH_MAX_K 8192u
+
+MIH_API mih_status mih_knn(const mih_index *index, const uint64_t *queries, uint32_t nq,
+                   const uint32_t *k, uint32_t k_uniform, const uint64_t *out_offsets,
+                   uint32_t *out_ids, int32_t *out_dist, uint64_t *query_stats,
+                   mih_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------
+ * mih_rnear -- Algorithm 2 (Sec. 2.2): all codes within r bits of each query.
+ *
+ * With r = m r' + a, tables 1..a+1 are searched to radius r' and the others
+ * to r' - 1; the union is culled by the full-code distance.
+ * r            0 <= r; r >= q returns the whole database.
+ * capacity     number of (id, dist) slots in out_ids / out_dist.
+ * out_offsets  device uint64[nq+1]: CSR offsets of the results, always
+ *              written (also on MIH_EOVERFLOW, so the caller can allocate
+ *              out_offsets[nq] slots and call again).
+ * out_ids, out_dist  device, `capacity` slots, may be NULL when capacity is 0.
+ * total        host, nullable: total number of results.
+ * query_stats, stats  as in mih_knn (last step = r).
+ * Synchronises `stream`.
+ * Errors: MIH_EOVERFLOW when the total exceeds capacity (nothing written to
+ * out_ids / out_dist), MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA.
+ */
+MIH_API mih_status mih_rnear(const mih_index *index, const uint64_t *queries, uint32_t nq, int r,
+                     uint64_t capacity, uint64_t *out_offsets, uint32_t *out_ids,
+                     int32_t *out_dist, uint64_t *total, uint64_t *query_stats,
+                     mih_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------------
+ * linscan_knn -- the linear-scan baseline (Sec. 5.2): exact k-NN of each
+ * query by computing the Hamming distance to every code (one xor per 64 bits
+ * and a population count, Sec. 6 "Hamming Distance").
+ *
+ * Arguments as in mih_build (codes, n, q) and mih_knn (queries ... out_dist);
+ * the codes are only read during the call.  Synchronises `stream`.
+ * Errors: MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA.
+ */
+MIH_API mih_status linscan_knn(const uint64_t *codes, uint64_t n, int q, const uint64_t *queries,
+                       uint32_t nq, const uint32_t *k, uint32_t k_uniform,
+                       const uint64_t *out_offsets, uint32_t *out_ids, int32_t *out_dist,
+                       void *stream);
+
+/* ------------------------------------------------------------------------
+ * Host-only helpers (no GPU needed).
+ */
+
+/* Substring layout of Sec. 2.1 (footnote): writes m offsets and lengths
+ * (host arrays).  Errors: MIH_EINVAL when q < 1, m < 1 or m > q. */
+MIH_API mih_status mih_substring_layout(int q, int m, int32_t *offset, int32_t *length);
+
+/* Cost model of Eq. 7 (Sec. 3.1) in units of one lookup, for q-bit uniform
+ * codes, n codes, substring length s and search radius r:
+ * (1 + n / 2^s) (q / s) sum_{z <= floor(s r / q)} C(s, z). */
+MIH_API double mih_cost_model(int q, uint64_t n, int s, int r);
+
+/* Number of substrings suggested by Sec. 3.1 / Table 4: the integer closest
+ * to q / log2(n), clamped so that no substring exceeds 32 bits and m <= q. */
+MIH_API int mih_suggest_m(int q, uint64_t n);
+
+/* Static text of a status code. */
+MIH_API const char *mih_status_str(mih_status s);
+
+/* Detail of the last error raised on the calling host thread ("" if none). */
+MIH_API const char *mih_last_error(void);
+
+/* Library version string. */
+MIH_API const char *mih_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MIH_H_ */

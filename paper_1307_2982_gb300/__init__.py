@@ -1,0 +1,297 @@
+"""Exact k-NN and r-neighbour search in Hamming space by multi-index hashing
+on one GB300 GPU (sm_103a).
+
+Thin ctypes binding over the C-ABI of ``include/mih.h`` (library
+``libmih.so``, built in-tree by :func:`build`).  The functions keep the C
+names; they only marshal arguments (torch CUDA tensors -> device pointers,
+the current torch stream -> ``cudaStream_t``) and turn a non-OK status into
+:class:`MihError`.  Every step of the search runs in the library's CUDA
+kernels; there is no CPU path.
+
+Method: Norouzi, Punjani & Fleet, "Fast Exact Search in Hamming Space with
+Multi-Index Hashing" (arXiv:1307.2982).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmih.so")
+_lib = None
+
+MIH_OK, MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EOVERFLOW, MIH_ETIMEOUT, MIH_EINTERNAL = range(7)
+MIH_TABLE_AUTO, MIH_TABLE_DIRECT, MIH_TABLE_SPARSE = 0, 1, 2
+MIH_MAX_K = 8192
+PAD_ID = 0xFFFFFFFF
+
+EXPORTS = (
+    "mih_build", "mih_free", "mih_index_get_info", "mih_knn", "mih_rnear", "linscan_knn",
+    "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
+    "mih_last_error", "mih_version",
+)
+
+
+class MihError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class mih_params(ctypes.Structure):
+    _fields_ = [("table_kind", ctypes.c_int32), ("reserved", ctypes.c_int32 * 15)]
+
+
+class mih_stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in (
+        "lookups", "candidates_raw", "candidates_unique", "steps", "phase2_queries", "waves")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class mih_index_info(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int32), ("m", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("substring_offset", ctypes.c_int32 * 256), ("substring_length", ctypes.c_int32 * 256),
+                ("table_kind", ctypes.c_int32 * 256), ("n", ctypes.c_uint64),
+                ("distinct_keys", ctypes.c_uint64 * 256), ("max_bucket", ctypes.c_uint64 * 256),
+                ("index_bytes", ctypes.c_uint64)]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from . import build_ext
+
+    return build_ext.build(force=force, verbose=verbose)
+
+
+def load():
+    """Load libmih.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_1307_2982_gb300.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    st = ctypes.c_int
+    lib.mih_build.argtypes = [P, u64, i32, i32, P, P, ctypes.POINTER(P)]
+    lib.mih_build.restype = st
+    lib.mih_free.argtypes = [P]
+    lib.mih_free.restype = None
+    lib.mih_index_get_info.argtypes = [P, P]
+    lib.mih_index_get_info.restype = st
+    lib.mih_knn.argtypes = [P, P, u32, P, u32, P, P, P, P, P, P]
+    lib.mih_knn.restype = st
+    lib.mih_rnear.argtypes = [P, P, u32, i32, u64, P, P, P, ctypes.POINTER(u64), P, P, P]
+    lib.mih_rnear.restype = st
+    lib.linscan_knn.argtypes = [P, u64, i32, P, u32, P, u32, P, P, P, P]
+    lib.linscan_knn.restype = st
+    lib.mih_substring_layout.argtypes = [i32, i32, P, P]
+    lib.mih_substring_layout.restype = st
+    lib.mih_cost_model.argtypes = [i32, u64, i32, i32]
+    lib.mih_cost_model.restype = ctypes.c_double
+    lib.mih_suggest_m.argtypes = [i32, u64]
+    lib.mih_suggest_m.restype = i32
+    lib.mih_status_str.argtypes = [st]
+    lib.mih_status_str.restype = ctypes.c_char_p
+    lib.mih_last_error.argtypes = []
+    lib.mih_last_error.restype = ctypes.c_char_p
+    lib.mih_version.argtypes = []
+    lib.mih_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != MIH_OK:
+        lib = load()
+        detail = lib.mih_last_error().decode() or lib.mih_status_str(status).decode()
+        raise MihError(status, where, detail)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _codes_arg(codes, q: int):
+    """(n, q/64) int64/uint64 CUDA tensor -> (pointer, n)."""
+    if not codes.is_cuda:
+        raise ValueError("codes must be a CUDA tensor")
+    if codes.dim() != 2 or codes.shape[1] * 64 != q or not codes.is_contiguous():
+        raise ValueError(f"codes must be a contiguous (n, {q // 64}) tensor")
+    if codes.element_size() != 8:
+        raise ValueError("codes must have 8-byte elements (int64 or uint64 bit patterns)")
+    return _ptr(codes), codes.shape[0]
+
+
+# ----------------------------------------------------------------- host-only
+def mih_status_str(status: int) -> str:
+    return load().mih_status_str(status).decode()
+
+
+def mih_last_error() -> str:
+    return load().mih_last_error().decode()
+
+
+def mih_version() -> str:
+    return load().mih_version().decode()
+
+
+def mih_substring_layout(q: int, m: int):
+    off = (ctypes.c_int32 * max(m, 1))()
+    ln = (ctypes.c_int32 * max(m, 1))()
+    _check(load().mih_substring_layout(q, m, off, ln), "mih_substring_layout")
+    return list(off)[:m], list(ln)[:m]
+
+
+def mih_cost_model(q: int, n: int, s: int, r: int) -> float:
+    return float(load().mih_cost_model(q, n, s, r))
+
+
+def mih_suggest_m(q: int, n: int) -> int:
+    return int(load().mih_suggest_m(q, n))
+
+
+# ------------------------------------------------------------------- index
+class MihIndex:
+    """Owns a ``mih_index*``; keeps the borrowed code tensor alive."""
+
+    def __init__(self, handle, codes, q: int, m: int):
+        self.handle = handle
+        self.codes = codes
+        self.q, self.m = q, m
+        self.n = codes.shape[0]
+
+    def info(self) -> dict:
+        inf = mih_index_info()
+        _check(load().mih_index_get_info(self.handle, ctypes.byref(inf)), "mih_index_get_info")
+        m = inf.m
+        return {
+            "q": inf.q, "m": m, "n": int(inf.n), "index_bytes": int(inf.index_bytes),
+            "substring_offset": list(inf.substring_offset)[:m],
+            "substring_length": list(inf.substring_length)[:m],
+            "table_kind": list(inf.table_kind)[:m],
+            "distinct_keys": [int(x) for x in list(inf.distinct_keys)[:m]],
+            "max_bucket": [int(x) for x in list(inf.max_bucket)[:m]],
+        }
+
+    def free(self):
+        if self.handle:
+            load().mih_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, stream=None) -> MihIndex:
+    ptr, n = _codes_arg(codes, q)
+    p = mih_params()
+    p.table_kind = table_kind
+    h = ctypes.c_void_p()
+    _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
+    return MihIndex(h, codes, q, m)
+
+
+def mih_free(index: MihIndex):
+    index.free()
+
+
+def _k_args(nq, k, device):
+    """Uniform int k or a per-query CUDA uint32/int32 tensor -> C arguments."""
+    import torch
+
+    if isinstance(k, int):
+        return None, k, None, (nq, k)
+    kt = k if k.is_cuda else k.to(device)
+    kt = kt.to(torch.int32).contiguous()
+    off = torch.zeros(nq + 1, dtype=torch.int64, device=device)
+    off[1:] = torch.cumsum(kt.to(torch.int64), 0)
+    return kt, 0, off, (int(off[-1].item()),)
+
+
+def mih_knn(index: MihIndex, queries, k, stream=None, query_stats: bool = False, out=None):
+    """Exact k-NN (Alg. 3).  Returns (ids int32-view of uint32, dist, [offsets], stats dict[, qstats])."""
+    import torch
+
+    qptr, nq = _codes_arg(queries, index.q)
+    kt, ku, off, shape = _k_args(nq, k, queries.device)
+    if out is None:
+        ids = torch.empty(shape, dtype=torch.int32, device=queries.device)
+        dist = torch.empty(shape, dtype=torch.int32, device=queries.device)
+    else:
+        ids, dist = out
+    qs = torch.empty((nq, 4), dtype=torch.int64, device=queries.device) if query_stats else None
+    st = mih_stats()
+    _check(load().mih_knn(index.handle, qptr, nq, _ptr(kt), ku, _ptr(off), _ptr(ids), _ptr(dist), _ptr(qs),
+                          ctypes.byref(st), _stream(stream)), "mih_knn")
+    res = {"ids": ids, "dist": dist, "stats": st.as_dict()}
+    if off is not None:
+        res["offsets"] = off
+    if qs is not None:
+        res["query_stats"] = qs
+    return res
+
+
+def mih_rnear(index: MihIndex, queries, r: int, capacity: int | None = None, stream=None,
+              query_stats: bool = False):
+    """All codes within r bits (Alg. 2), CSR (offsets, ids, dist) in (distance, id) order.
+
+    With capacity None the call sizes the output itself (count call, then fill)."""
+    import torch
+
+    qptr, nq = _codes_arg(queries, index.q)
+    dev = queries.device
+    off = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    qs = torch.empty((nq, 4), dtype=torch.int64, device=dev) if query_stats else None
+    lib = load()
+    total = ctypes.c_uint64(0)
+    st = mih_stats()
+    if capacity is None:
+        s = lib.mih_rnear(index.handle, qptr, nq, r, 0, _ptr(off), None, None, ctypes.byref(total), None, None,
+                          _stream(stream))
+        if s not in (MIH_OK, MIH_EOVERFLOW):
+            _check(s, "mih_rnear")
+        capacity = int(total.value)
+    ids = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    dist = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    _check(lib.mih_rnear(index.handle, qptr, nq, r, capacity, _ptr(off), _ptr(ids), _ptr(dist),
+                         ctypes.byref(total), _ptr(qs), ctypes.byref(st), _stream(stream)), "mih_rnear")
+    t = int(total.value)
+    res = {"offsets": off, "ids": ids[:t], "dist": dist[:t], "total": t, "stats": st.as_dict()}
+    if qs is not None:
+        res["query_stats"] = qs
+    return res
+
+
+def linscan_knn(codes, q: int, queries, k, stream=None, out=None):
+    """Exact k-NN by linear scan (Sec. 5.2 baseline)."""
+    import torch
+
+    cptr, n = _codes_arg(codes, q)
+    qptr, nq = _codes_arg(queries, q)
+    kt, ku, off, shape = _k_args(nq, k, queries.device)
+    if out is None:
+        ids = torch.empty(shape, dtype=torch.int32, device=queries.device)
+        dist = torch.empty(shape, dtype=torch.int32, device=queries.device)
+    else:
+        ids, dist = out
+    _check(load().linscan_knn(cptr, n, q, qptr, nq, _ptr(kt), ku, _ptr(off), _ptr(ids), _ptr(dist),
+                              _stream(stream)), "linscan_knn")
+    res = {"ids": ids, "dist": dist}
+    if off is not None:
+        res["offsets"] = off
+    return res

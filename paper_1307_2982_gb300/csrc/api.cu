@@ -1,0 +1,219 @@
+// api.cu -- host-side entry points that need no kernels: status text, error
+// detail, the scratch pool, substring layout and the cost-model helpers.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "launch.h"
+
+namespace mih {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+// ------------------------------------------------------------ scratch pool
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+DeviceInfo g_dev[kMaxDevices] = {};
+bool g_dev_ok[kMaxDevices] = {};
+
+mih_status pool_for_current(cudaMemPool_t* out) {
+    int dev = 0;
+    MIH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal %d out of range", dev);
+        return MIH_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        MIH_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t thr = UINT64_MAX;
+        MIH_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return MIH_OK;
+}
+}  // namespace
+
+mih_status Workspace::raw_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaMemPool_t pool;
+    MIH_TRY(pool_for_current(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, stream_);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("scratch allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? MIH_ENOMEM : MIH_ECUDA;
+    }
+    ptrs_.push_back(*p);
+    return MIH_OK;
+}
+
+void Workspace::release(void* p) {
+    for (size_t i = 0; i < ptrs_.size(); ++i) {
+        if (ptrs_[i] == p) {
+            cudaFreeAsync(p, stream_);
+            ptrs_[i] = ptrs_.back();
+            ptrs_.pop_back();
+            return;
+        }
+    }
+}
+
+Workspace::~Workspace() {
+    for (void* p : ptrs_) cudaFreeAsync(p, stream_);
+}
+
+mih_status trim_pool() {
+    cudaMemPool_t pool;
+    MIH_TRY(pool_for_current(&pool));
+    MIH_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return MIH_OK;
+}
+
+mih_status check_device_ptr(const void* p, const char* what) {
+    if (!p) {
+        set_error("%s is NULL", what);
+        return MIH_EINVAL;
+    }
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("%s: cudaPointerGetAttributes failed: %s", what, cudaGetErrorString(e));
+        return MIH_EINVAL;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) {
+        set_error("%s must be CUDA device memory", what);
+        return MIH_EINVAL;
+    }
+    int dev = 0;
+    MIH_CUDA(cudaGetDevice(&dev));
+    if (a.type == cudaMemoryTypeDevice && a.device != dev) {
+        set_error("%s lives on device %d, current device is %d", what, a.device, dev);
+        return MIH_EINVAL;
+    }
+    return MIH_OK;
+}
+
+mih_status check_code_alignment(const void* p, int W, const char* what) {
+    const uintptr_t need = W >= 2 ? 16 : 8;
+    if (reinterpret_cast<uintptr_t>(p) % need != 0) {
+        set_error("%s must be %u-byte aligned", what, static_cast<unsigned>(need));
+        return MIH_EINVAL;
+    }
+    return MIH_OK;
+}
+
+mih_status device_info(DeviceInfo* out) {
+    int dev = 0;
+    MIH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device ordinal %d out of range", dev);
+        return MIH_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (g_dev_ok[dev]) {
+            *out = g_dev[dev];
+            return MIH_OK;
+        }
+    }
+    DeviceInfo d;
+    d.device = dev;
+    MIH_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    MIH_CUDA(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    g_dev[dev] = d;
+    g_dev_ok[dev] = true;
+    *out = d;
+    return MIH_OK;
+}
+
+}  // namespace mih
+
+// ------------------------------------------------------------------ C-ABI
+extern "C" {
+
+const char* mih_status_str(mih_status s) {
+    switch (s) {
+        case MIH_OK: return "MIH_OK";
+        case MIH_EINVAL: return "MIH_EINVAL: invalid argument";
+        case MIH_ENOMEM: return "MIH_ENOMEM: device memory allocation failed";
+        case MIH_ECUDA: return "MIH_ECUDA: CUDA runtime error";
+        case MIH_EOVERFLOW: return "MIH_EOVERFLOW: result capacity exceeded";
+        case MIH_ETIMEOUT: return "MIH_ETIMEOUT: bounded device wait expired";
+        case MIH_EINTERNAL: return "MIH_EINTERNAL: internal consistency check failed";
+    }
+    return "unknown mih_status";
+}
+
+const char* mih_last_error(void) { return mih::g_err; }
+
+const char* mih_version(void) { return "mih-gb300 0.1 (sm_103a)"; }
+
+// Sec. 2.1 footnote: substrings of floor(q/m) or ceil(q/m) bits; the first
+// m - (q mod m) are the short ones.
+mih_status mih_substring_layout(int q, int m, int32_t* offset, int32_t* length) {
+    if (q < 1 || m < 1 || m > q || !offset || !length) {
+        mih::set_error("substring layout: need 1 <= m <= q and non-null outputs (q=%d m=%d)", q, m);
+        return MIH_EINVAL;
+    }
+    const int shortl = q / m, nlong = q % m;
+    int o = 0;
+    for (int j = 0; j < m; ++j) {
+        length[j] = shortl + (j >= m - nlong ? 1 : 0);
+        offset[j] = o;
+        o += length[j];
+    }
+    return MIH_OK;
+}
+
+// Eq. 7: cost(s) = (1 + n / 2^s) (q / s) sum_{z=0}^{floor(s r / q)} C(s, z).
+double mih_cost_model(int q, uint64_t n, int s, int r) {
+    if (q < 1 || s < 1 || s > q || r < 0) return -1.0;
+    const int zmax = static_cast<int>((static_cast<int64_t>(s) * r) / q);
+    double ball = 0.0, c = 1.0;
+    for (int z = 0; z <= zmax && z <= s; ++z) {
+        ball += c;
+        c = c * (s - z) / (z + 1);
+    }
+    return (1.0 + static_cast<double>(n) / ldexp(1.0, s)) * (static_cast<double>(q) / s) * ball;
+}
+
+// Sec. 3.1 / Table 4: m close to q / log2(n); no substring above 32 bits.
+int mih_suggest_m(int q, uint64_t n) {
+    if (q < 1) return 0;
+    int m = (n > 1) ? static_cast<int>(lround(q / log2(static_cast<double>(n)))) : q;
+    const int mmin = (q + 31) / 32;
+    if (m < mmin) m = mmin;
+    if (m > q) m = q;
+    if (m < 1) m = 1;
+    return m;
+}
+
+}  // extern "C"

@@ -1,0 +1,440 @@
+// linscan.cu -- the linear-scan baseline (Sec. 5.2): exact k-NN by computing
+// the Hamming distance from each query to every code (Sec. 6 "Hamming
+// Distance": xor and population count per 64 bits).
+//
+// Batched design.  A CTA holds a tile of queries in shared memory and streams
+// a contiguous range of codes; each thread keeps a few codes in registers and
+// runs them against every query of the tile.  A pair is kept only if its
+// distance is at most the query's running bound thr_q on the k-th smallest
+// distance; kept pairs go to a bounded per-query buffer and a per-query
+// distance histogram in global memory, from which every CTA periodically
+// tightens thr_q (thr_q = the smallest D with at least min(k, n) kept codes
+// within D bits, always >= the true k-th distance).  The initial bound comes
+// from an exact histogram over a prefix sample of the database.
+//
+// Most pairs are far from the bound, so the kernel first tests a cheaper
+// lower bound: the popcount of the OR of G consecutive 32-bit words of
+// (code xor query) never exceeds their total popcount.  Only pairs that pass
+// it pay for the exact distance.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "launch.h"
+#include "mih_internal.cuh"
+#include "search.h"
+
+namespace mih {
+namespace {
+
+constexpr int kLsThreads = 256;
+constexpr int kLsCodesPerThread = 4;                       // J
+constexpr int kLsTile = kLsThreads * kLsCodesPerThread;    // codes per tile
+constexpr int kLsQueries = 64;                             // queries per CTA
+constexpr int kLsRefresh = 8;                              // tiles between bound refreshes
+constexpr uint32_t kSampleMax = 1u << 18;                  // prefix sample for the first bound
+
+struct ScanArgs {
+    const uint64_t* codes;
+    uint64_t n;
+    const uint64_t* queries;
+    uint32_t nq;
+    int qbits;
+    const uint32_t* kq;
+    uint32_t k_uniform;
+    uint64_t split_len;        // codes per CTA column (multiple of kLsTile)
+    int32_t* thr;              // [nq] running bound (read at start, written by refresh)
+    uint32_t* hist;            // [nq][q+1] kept distances (first pass)
+    uint64_t* buf;             // first pass: [nq][cap]; second pass: entries at base[q]
+    uint32_t cap;
+    uint32_t* cnt;             // first pass: kept count; second pass: cursor
+    const uint64_t* base;      // second pass only: [nq + 1]
+    int second_pass;
+    int* err;                  // set when a second-pass write would leave its query's range
+};
+
+__device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform, uint32_t q, uint64_t n) {
+    const uint64_t k = kq ? kq[q] : k_uniform;
+    return static_cast<uint32_t>(k < n ? k : n);
+}
+
+// Lower bound on popcount(x) from ORs of G consecutive 32-bit words.
+template <int W, int G>
+__device__ __forceinline__ int or_bound(const uint64_t (&x)[W]) {
+    if constexpr (G == 1) {
+        int d = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) d += __popcll(x[w]);
+        return d;
+    } else if constexpr (G == 2) {
+        int d = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            d += __popc(static_cast<uint32_t>(x[w]) | static_cast<uint32_t>(x[w] >> 32));
+        return d;
+    } else {
+        constexpr int per = G / 2;  // 64-bit words per group
+        int d = 0;
+#pragma unroll
+        for (int grp = 0; grp < W / per; ++grp) {
+            uint64_t o = 0;
+#pragma unroll
+            for (int w = 0; w < per; ++w) o |= x[grp * per + w];
+            d += __popc(static_cast<uint32_t>(o) | static_cast<uint32_t>(o >> 32));
+        }
+        return d;
+    }
+}
+
+template <int W, int G>
+__global__ void __launch_bounds__(kLsThreads) linscan_kernel(ScanArgs a) {
+    __shared__ uint64_t s_q[kLsQueries][W];
+    __shared__ int s_thr[kLsQueries];
+    const uint32_t q0 = blockIdx.x * kLsQueries;
+    const uint32_t nql = min(static_cast<uint32_t>(kLsQueries), a.nq - q0);
+    for (int i = threadIdx.x; i < kLsQueries * W; i += blockDim.x) {
+        const int qi = i / W, w = i % W;
+        s_q[qi][w] = (static_cast<uint32_t>(qi) < nql) ? a.queries[static_cast<uint64_t>(q0 + qi) * W + w] : 0ull;
+    }
+    for (int i = threadIdx.x; i < kLsQueries; i += blockDim.x)
+        s_thr[i] = (static_cast<uint32_t>(i) < nql) ? a.thr[q0 + i] : -1;
+    __syncthreads();
+    const uint64_t begin = static_cast<uint64_t>(blockIdx.y) * a.split_len;
+    const uint64_t end = min(a.n, begin + a.split_len);
+    int tile_no = 0;
+    for (uint64_t t0 = begin; t0 < end; t0 += kLsTile, ++tile_no) {
+        uint64_t c[kLsCodesPerThread][W];
+        uint64_t idx[kLsCodesPerThread];
+#pragma unroll
+        for (int jj = 0; jj < kLsCodesPerThread; ++jj) {
+            idx[jj] = t0 + static_cast<uint64_t>(jj) * kLsThreads + threadIdx.x;
+            const Code<W> v = (idx[jj] < end) ? load_code<W>(a.codes, idx[jj]) : Code<W>{};
+#pragma unroll
+            for (int w = 0; w < W; ++w) c[jj][w] = v.w[w];
+        }
+        for (uint32_t qi = 0; qi < nql; ++qi) {
+            uint64_t g[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) g[w] = s_q[qi][w];
+            const int th = s_thr[qi];
+#pragma unroll
+            for (int jj = 0; jj < kLsCodesPerThread; ++jj) {
+                uint64_t x[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) x[w] = c[jj][w] ^ g[w];
+                const int lb = or_bound<W, G>(x);
+                if (lb <= th && idx[jj] < end) {
+                    int d = lb;
+                    if constexpr (G != 1) d = or_bound<W, 1>(x);
+                    if (d <= th) {
+                        const uint32_t q = q0 + qi;
+                        const uint32_t p = atomicAdd(&a.cnt[q], 1u);
+                        if (!a.second_pass) {
+                            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, static_cast<uint32_t>(idx[jj]));
+                            atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.qbits + 1) + d], 1u);
+                        } else {
+                            const uint64_t slot = a.base[q] + p;
+                            if (slot < a.base[q + 1]) a.buf[slot] = pack_entry(d, static_cast<uint32_t>(idx[jj]));
+                            else atomicExch(a.err, 1);
+                        }
+                    }
+                }
+            }
+        }
+        if (!a.second_pass && (tile_no % kLsRefresh) == kLsRefresh - 1) {
+            __syncthreads();
+            if (threadIdx.x < nql) {
+                const uint32_t q = q0 + threadIdx.x;
+                const uint32_t kk = kk_of(a.kq, a.k_uniform, q, a.n);
+                const uint32_t* h = a.hist + static_cast<uint64_t>(q) * (a.qbits + 1);
+                const int old = s_thr[threadIdx.x];
+                uint32_t cum = 0;
+                for (int d = 0; d < old; ++d) {
+                    cum += __ldcg(h + d);  // written by other CTAs' atomics: bypass L1
+                    if (cum >= kk) {
+                        s_thr[threadIdx.x] = d;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Exact distance histogram of the first S codes per query (one warp per
+// query, lane-private columns in shared memory), then the bound: the smallest
+// D with at least min(k, n) sample codes within D bits (q if S < min(k, n)).
+template <int W>
+__global__ void __launch_bounds__(128) sample_bound_kernel(const uint64_t* __restrict__ codes, uint64_t S,
+                                                           const uint64_t* __restrict__ queries, uint32_t nq,
+                                                           int qbits, const uint32_t* kq, uint32_t k_uniform,
+                                                           uint64_t n, int32_t* __restrict__ thr) {
+    extern __shared__ uint16_t s_h[];  // [warps][qbits+1][32]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t q = blockIdx.x * (blockDim.x >> 5) + warp;
+    uint16_t* h = s_h + static_cast<size_t>(warp) * (qbits + 1) * 32;
+    for (int d = 0; d <= qbits; ++d) h[d * 32 + lane] = 0;
+    __syncwarp();
+    if (q >= nq) return;
+    Code<W> g;
+#pragma unroll
+    for (int w = 0; w < W; ++w) g.w[w] = queries[static_cast<uint64_t>(q) * W + w];
+    for (uint64_t i = lane; i < S; i += 32) {
+        const Code<W> c = load_code<W>(codes, i);
+        const int d = hamming<W>(c, g);
+        h[d * 32 + lane] += 1;
+    }
+    __syncwarp();
+    const uint32_t kk = kk_of(kq, k_uniform, q, n);
+    uint32_t cum = 0;
+    int bound = qbits;
+    for (int d0 = 0; d0 <= qbits; d0 += 32) {
+        const int d = d0 + lane;
+        uint32_t v = 0;
+        if (d <= qbits)
+            for (int l = 0; l < 32; ++l) v += h[d * 32 + l];
+        const uint32_t incl = warp_inclusive_scan(v);
+        const uint32_t reach = __ballot_sync(0xFFFFFFFFu, d <= qbits && cum + incl >= kk);
+        if (reach) {
+            bound = d0 + __ffs(reach) - 1;
+            break;
+        }
+        cum += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    if (lane == 0) thr[q] = bound;
+}
+
+// d_k from the kept-distance histogram (exact up to d_k); overflowed queries
+// get their exact buffer size and thr = d_k for the second pass, the others
+// thr = -1 (skipped).
+__global__ void finish_first_pass_kernel(uint32_t nq, int qbits, uint64_t n, const uint32_t* kq, uint32_t k_uniform,
+                                         const uint32_t* __restrict__ hist, const uint32_t* __restrict__ cnt,
+                                         uint32_t cap, int32_t* __restrict__ dk, int32_t* __restrict__ thr,
+                                         uint64_t* __restrict__ need, unsigned int* __restrict__ n_over) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x) {
+        if (q == nq) { need[q] = 0; continue; }
+        const uint32_t kk = kk_of(kq, k_uniform, q, n);
+        const uint32_t* h = hist + static_cast<uint64_t>(q) * (qbits + 1);
+        uint64_t cum = 0;
+        int d = 0;
+        for (; d <= qbits; ++d) {
+            cum += h[d];
+            if (cum >= kk) break;
+        }
+        if (d > qbits) d = qbits;
+        dk[q] = d;
+        const bool over = cnt[q] > cap;
+        need[q] = over ? cum : 0;
+        thr[q] = over ? d : -1;
+        if (over) atomicAdd(n_over, 1u);
+    }
+}
+
+unsigned grid1(uint64_t n) {
+    uint64_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    return static_cast<unsigned>(g ? g : 1);
+}
+
+template <int W>
+mih_status launch_sample(const uint64_t* codes, uint64_t S, const uint64_t* queries, uint32_t nq, int qbits,
+                         const uint32_t* kq, uint32_t k_uniform, uint64_t n, int32_t* thr, cudaStream_t s) {
+    const int warps = 4;
+    const size_t smem = static_cast<size_t>(warps) * (qbits + 1) * 32 * sizeof(uint16_t);
+    if (smem > 48 * 1024)
+        MIH_CUDA(cudaFuncSetAttribute(sample_bound_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+    sample_bound_kernel<W><<<(nq + warps - 1) / warps, warps * 32, smem, s>>>(codes, S, queries, nq, qbits, kq,
+                                                                              k_uniform, n, thr);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
+template <int W, int G>
+mih_status launch_scan_wg(const ScanArgs& a, dim3 grid, cudaStream_t s) {
+    linscan_kernel<W, G><<<grid, kLsThreads, 0, s>>>(a);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
+template <int W>
+mih_status launch_scan_w(const ScanArgs& a, int G, dim3 grid, cudaStream_t s) {
+    if (G >= 4 && W >= 2) return launch_scan_wg<W, (W >= 2 ? 4 : 2)>(a, grid, s);
+    if (G >= 2) return launch_scan_wg<W, 2>(a, grid, s);
+    return launch_scan_wg<W, 1>(a, grid, s);
+}
+
+mih_status launch_scan(const ScanArgs& a, int W, int G, dim3 grid, cudaStream_t s) {
+    if (W == 1) return launch_scan_w<1>(a, G, grid, s);
+    if (W == 2) return launch_scan_w<2>(a, G, grid, s);
+    return launch_scan_w<4>(a, G, grid, s);
+}
+
+// OR-group width: the widest G whose expected lower bound on a random pair,
+// (2W/G) * 32 * (1 - 2^-G), stays clear of the typical first bound.
+int choose_group(int W, int typical_thr) {
+    int best = 1;
+    for (int G = 2; G <= 4 && G <= 2 * W; G *= 2) {
+        const double e = (2.0 * W / G) * 32.0 * (1.0 - 1.0 / (1 << G));
+        if (e > typical_thr + 6) best = G;
+    }
+    return best;
+}
+
+}  // namespace
+}  // namespace mih
+
+using namespace mih;
+
+extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, const uint64_t* queries, uint32_t nq,
+                                  const uint32_t* k, uint32_t k_uniform, const uint64_t* out_offsets,
+                                  uint32_t* out_ids, int32_t* out_dist, void* stream) {
+    clear_error();
+    if (q != 64 && q != 128 && q != 256) {
+        set_error("linscan_knn: q must be 64, 128 or 256 (got %d)", q);
+        return MIH_EINVAL;
+    }
+    if (n >= 0xFFFFFFFFull) {
+        set_error("linscan_knn: n must be below 2^32 - 1");
+        return MIH_EINVAL;
+    }
+    if (nq > (1u << 23)) {
+        set_error("linscan_knn: nq must be at most 2^23");
+        return MIH_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    uint32_t kmax = 0;
+    MIH_TRY(check_k_args(nq, k, k_uniform, out_offsets, out_ids, out_dist, &kmax, ws));
+    if (nq == 0) return MIH_OK;
+    MIH_TRY(check_device_ptr(queries, "queries"));
+    if (n > 0) {
+        MIH_TRY(check_device_ptr(codes, "codes"));
+        MIH_TRY(check_code_alignment(codes, q / 64, "codes"));
+    }
+    DeviceInfo dev;
+    MIH_TRY(device_info(&dev));
+    const int W = q / 64;
+    const uint32_t cap = std::max<uint32_t>(16384u, std::min<uint32_t>(16u * kmax, 65536u));
+
+    int32_t *thr, *dk;
+    uint32_t *hist, *cnt;
+    uint64_t *buf, *need;
+    unsigned int* n_over;
+    MIH_TRY(ws.alloc(&thr, nq));
+    MIH_TRY(ws.alloc(&dk, nq));
+    MIH_TRY(ws.alloc(&hist, static_cast<size_t>(nq) * (q + 1)));
+    MIH_TRY(ws.alloc(&cnt, nq));
+    MIH_TRY(ws.alloc(&buf, static_cast<size_t>(nq) * cap));
+    MIH_TRY(ws.alloc(&need, static_cast<size_t>(nq) + 1));
+    MIH_TRY(ws.alloc(&n_over, 1));
+    MIH_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nq * (q + 1), s));
+    MIH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nq, s));
+    MIH_CUDA(cudaMemsetAsync(n_over, 0, sizeof(unsigned int), s));
+
+    uint64_t* buf2 = nullptr;
+    unsigned int hover = 0;
+    if (n > 0) {
+        const uint64_t S = std::min<uint64_t>(n, kSampleMax);
+        if (W == 1) MIH_TRY(launch_sample<1>(codes, S, queries, nq, q, k, k_uniform, n, thr, s));
+        else if (W == 2) MIH_TRY(launch_sample<2>(codes, S, queries, nq, q, k, k_uniform, n, thr, s));
+        else MIH_TRY(launch_sample<4>(codes, S, queries, nq, q, k, k_uniform, n, thr, s));
+        // typical first bound -> OR-group width
+        std::vector<int32_t> hthr(nq);
+        MIH_CUDA(cudaMemcpyAsync(hthr.data(), thr, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        std::nth_element(hthr.begin(), hthr.begin() + nq / 2, hthr.end());
+        const int G = choose_group(W, hthr[nq / 2]);
+
+        const uint32_t qtiles = (nq + kLsQueries - 1) / kLsQueries;
+        // enough CTA columns to fill the GPU about 4 times over
+        uint64_t target = static_cast<uint64_t>(dev.sms) * 4;
+        uint64_t splits = (target + qtiles - 1) / qtiles;
+        const uint64_t max_splits = (n + kLsTile - 1) / kLsTile;
+        if (splits > max_splits) splits = max_splits;
+        if (splits < 1) splits = 1;
+        if (splits > 65535) splits = 65535;
+        uint64_t split_len = (n + splits - 1) / splits;
+        split_len = (split_len + kLsTile - 1) / kLsTile * kLsTile;
+        splits = (n + split_len - 1) / split_len;
+
+        ScanArgs a;
+        memset(&a, 0, sizeof(a));
+        a.codes = codes;
+        a.n = n;
+        a.queries = queries;
+        a.nq = nq;
+        a.qbits = q;
+        a.kq = k;
+        a.k_uniform = k_uniform;
+        a.split_len = split_len;
+        a.thr = thr;
+        a.hist = hist;
+        a.buf = buf;
+        a.cap = cap;
+        a.cnt = cnt;
+        const dim3 grid(qtiles, static_cast<unsigned>(splits));
+        MIH_TRY(launch_scan(a, W, G, grid, s));
+
+        finish_first_pass_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, q, n, k, k_uniform, hist, cnt, cap, dk, thr, need,
+                                                              n_over);
+        MIH_LAUNCH_CHECK();
+        MIH_CUDA(cudaMemcpyAsync(&hover, n_over, sizeof(hover), cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        if (hover > 0) {
+            // Second pass over the database for queries whose buffer overflowed:
+            // collect exactly the codes within d_k bits.
+            MIH_TRY(scan_exclusive_u64(need, need, static_cast<size_t>(nq) + 1, ws));
+            uint64_t total = 0;
+            MIH_CUDA(cudaMemcpyAsync(&total, need + nq, sizeof(total), cudaMemcpyDeviceToHost, s));
+            MIH_CUDA(cudaStreamSynchronize(s));
+            MIH_TRY(ws.alloc(&buf2, total));
+            uint32_t* cursor;
+            MIH_TRY(ws.alloc(&cursor, nq));
+            MIH_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, s));
+            int* err;
+            MIH_TRY(ws.alloc(&err, 1));
+            MIH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+            ScanArgs b = a;
+            b.buf = buf2;
+            b.cnt = cursor;
+            b.base = need;
+            b.second_pass = 1;
+            b.err = err;
+            MIH_TRY(launch_scan(b, W, 1, grid, s));
+            int herr = 0;
+            MIH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MIH_CUDA(cudaStreamSynchronize(s));
+            if (herr) {
+                set_error("linscan_knn: second pass found more codes within d_k than counted");
+                return MIH_EINTERNAL;
+            }
+        }
+    } else {
+        MIH_CUDA(cudaMemsetAsync(dk, 0, sizeof(int32_t) * nq, s));
+    }
+
+    SelectInputs si;
+    si.nq = nq;
+    si.n = n;
+    si.q = q;
+    si.kq = k;
+    si.k_uniform = k_uniform;
+    si.kmax = kmax;
+    si.out_off = out_offsets;
+    si.hist = hist;
+    si.dk = dk;
+    si.buf1 = buf;
+    si.cap = cap;
+    si.cnt1 = cnt;
+    si.buf2 = buf2;
+    si.base2 = need;
+    si.out_ids = out_ids;
+    si.out_dist = out_dist;
+    MIH_TRY(launch_select(si, ws));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    return MIH_OK;
+}

@@ -1,0 +1,195 @@
+// mih_internal.cuh -- device-side building blocks shared by the kernels of
+// the multi-index hashing library (sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mih.h"
+
+namespace mih {
+
+constexpr int kMaxTables = 256;
+constexpr uint32_t kPadId = 0xFFFFFFFFu;
+constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
+constexpr int kChunkKeys = 256;          // ring keys per work chunk (one warp)
+constexpr int kKeysPerLane = kChunkKeys / 32;
+constexpr uint32_t kBigBucket = 2048;    // buckets above this go to the big list
+
+// ---------------------------------------------------------------- tables
+// One substring hash table (Sec. 6): either direct-addressed CSR offsets over
+// all 2^s buckets, or a sparse form: the distinct keys in an open-addressing
+// index (4 slots of {key, rank} per 32-byte bucket) plus CSR begins by rank.
+struct TableDesc {
+    int32_t off;        // first code bit of the substring
+    int32_t len;        // s_j (1..32)
+    int32_t kind;       // MIH_TABLE_DIRECT / MIH_TABLE_SPARSE
+    int32_t pad_;
+    const uint32_t* ids;       // n ids ordered by (key, id)
+    const uint32_t* offsets;   // direct: offsets[2^s + 1]; sparse: begins[U + 1]
+    const uint2* slots;        // sparse: 4 * nbuckets slots {key, rank}
+    uint64_t bucket_mask;      // sparse: nbuckets - 1 (power of two)
+    uint32_t max_probe;        // sparse: longest probe sequence at build
+    uint32_t pad2_;
+};
+
+// ---------------------------------------------------------------- binomials
+// C(n, k) for 0 <= k <= n <= 32 (substrings hold at most 32 bits), built at
+// compile time (Pascal's rule) and read through the L1 cache: lanes of a warp
+// index it divergently, which a __constant__ bank would serialise.
+struct BinomTable {
+    uint64_t v[33][33];
+    constexpr BinomTable() : v() {
+        for (int a = 0; a <= 32; ++a) {
+            v[a][0] = 1;
+            for (int b = 1; b <= a; ++b) v[a][b] = v[a - 1][b - 1] + (b <= a - 1 ? v[a - 1][b] : 0);
+        }
+    }
+};
+
+static __device__ const BinomTable g_binom = BinomTable();
+
+__device__ __forceinline__ uint64_t binom(int n, int k) {
+    return (k < 0 || n < 0 || k > n) ? 0ull : __ldg(&g_binom.v[n][k]);
+}
+
+// ---------------------------------------------------------------- codes
+template <int W>
+struct Code {
+    uint64_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ Code<W> load_code(const uint64_t* __restrict__ codes, uint64_t i) {
+    Code<W> c;
+    const uint64_t* p = codes + i * W;
+    if constexpr (W == 1) {
+        c.w[0] = __ldg(p);
+    } else if constexpr (W == 2) {
+        ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        c.w[0] = v.x;
+        c.w[1] = v.y;
+    } else {
+        ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(p));
+        ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(p) + 1);
+        c.w[0] = a.x; c.w[1] = a.y; c.w[2] = b.x; c.w[3] = b.y;
+    }
+    return c;
+}
+
+template <int W>
+__device__ __forceinline__ int hamming(const Code<W>& a, const Code<W>& b) {
+    int d = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) d += __popcll(a.w[w] ^ b.w[w]);
+    return d;
+}
+
+// Bits [off, off + len) of a W-word code (len <= 32), bit 0 = code bit off.
+template <int W>
+__device__ __forceinline__ uint32_t substring_bits(const Code<W>& c, int off, int len) {
+    const int w0 = off >> 6, sh = off & 63;
+    uint64_t lo = 0, hi = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        if (w == w0) lo = c.w[w];
+        if (w == w0 + 1) hi = c.w[w];
+    }
+    uint64_t v = lo >> sh;
+    if (sh != 0 && sh + len > 64) v |= hi << (64 - sh);
+    const uint64_t mask = (len >= 64) ? ~0ull : ((1ull << len) - 1ull);
+    return static_cast<uint32_t>(v & mask);
+}
+
+// ---------------------------------------------------------------- rings
+// Keys at exactly rho bits from a query key are key ^ x with popcount(x) = rho
+// and x < 2^s (the bucket ring of one Alg. 3 step).  x runs through the
+// rho-subsets of {0..s-1} in increasing numeric order (colex order), so a
+// rank maps to a subset by the combinatorial number system and consecutive
+// ranks are one Gosper step apart.
+__device__ __forceinline__ uint64_t unrank_subset(uint64_t rank, int s, int rho) {
+    uint64_t x = 0;
+    int c = s;
+    for (int i = rho; i >= 1; --i) {
+        --c;
+        while (binom(c, i) > rank) --c;
+        rank -= binom(c, i);
+        x |= 1ull << c;
+    }
+    return x;
+}
+
+// Next larger integer with the same popcount (Gosper); x != 0.
+__device__ __forceinline__ uint64_t next_subset(uint64_t x) {
+    const uint64_t c = x & (0ull - x);
+    const uint64_t r = x + c;
+    return (((r ^ x) >> 2) >> (__ffsll(static_cast<long long>(c)) - 1)) | r;
+}
+
+// ---------------------------------------------------------------- lookup
+__device__ __forceinline__ uint32_t hash_key(uint32_t k) {
+    // 32-bit finaliser (xorshift-multiply), spreads clustered keys over buckets.
+    k ^= k >> 16;
+    k *= 0x7feb352dU;
+    k ^= k >> 15;
+    k *= 0x846ca68bU;
+    k ^= k >> 16;
+    return k;
+}
+
+// Bucket [begin, end) of `key` in table t (empty when absent).
+__device__ __forceinline__ void lookup_bucket(const TableDesc& t, uint32_t key, uint32_t& begin,
+                                              uint32_t& end) {
+    if (t.kind == MIH_TABLE_DIRECT) {
+        begin = __ldg(t.offsets + key);
+        end = __ldg(t.offsets + key + 1);
+        return;
+    }
+    uint64_t b = hash_key(key) & t.bucket_mask;
+    begin = end = 0;
+    for (uint32_t p = 0; p <= t.max_probe; ++p) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(t.slots + 4 * b);
+        const uint4 s01 = __ldg(s4);
+        const uint4 s23 = __ldg(s4 + 1);
+        uint32_t rank = kEmptySlot;
+        bool open = false;
+        if (s01.y != kEmptySlot) { if (s01.x == key) rank = s01.y; } else open = true;
+        if (rank == kEmptySlot && !open) {
+            if (s01.w != kEmptySlot) { if (s01.z == key) rank = s01.w; } else open = true;
+        }
+        if (rank == kEmptySlot && !open) {
+            if (s23.y != kEmptySlot) { if (s23.x == key) rank = s23.y; } else open = true;
+        }
+        if (rank == kEmptySlot && !open) {
+            if (s23.w != kEmptySlot) { if (s23.z == key) rank = s23.w; } else open = true;
+        }
+        if (rank != kEmptySlot) {
+            begin = __ldg(t.offsets + rank);
+            end = __ldg(t.offsets + rank + 1);
+            return;
+        }
+        if (open) return;
+        b = (b + 1) & t.bucket_mask;
+    }
+}
+
+// ---------------------------------------------------------------- warp utils
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane_id() >= static_cast<uint32_t>(o)) v += u;
+    }
+    return v;
+}
+
+// Packed result entry: distance in the high word so that uint64 order is
+// (distance, id) order.
+__device__ __forceinline__ uint64_t pack_entry(int d, uint32_t id) {
+    return (static_cast<uint64_t>(static_cast<uint32_t>(d)) << 32) | id;
+}
+
+}  // namespace mih

@@ -1,0 +1,1016 @@
+// search.cu -- multi-index hashing search on the GPU: Algorithm 3 (k-NN,
+// mih_knn) and Algorithm 2 (r-neighbours, mih_rnear), plus the k-selection
+// shared with the linear scan.
+//
+// Work model.  Step t of a query searches ring rho = floor(t/m) of table
+// j = t mod m: the C(s_j, rho) buckets whose key differs from the query's
+// j-th substring in exactly rho bits.  All codes within t bits of the query
+// have been found once steps 0..t are done (Prop. 2), so Alg. 2 at radius r
+// is steps 0..r and Alg. 3 stops after the first step t with at least
+// min(k, n) codes within t bits.  A query's pending steps are cut into chunks
+// of 256 ring keys; one warp takes one chunk: each lane unranks its first key
+// (combinatorial number system) and walks 8 keys by Gosper steps, looks the
+// buckets up, and the warp then shares out the union of the 32 buckets'
+// entries, verifies each candidate on the full code and bins it by
+// distance.  Buckets above 2048 entries are cut into slices that a second
+// kernel spreads over all warps.
+//
+// Duplicates (Sec. 6 "Duplicate Candidates") are removed without an n-bit
+// set: a code reached at step t = m rho + j is kept only if t is the first
+// step that reaches it, i.e. no table j' < j has substring distance <= rho
+// and no table j' > j has substring distance < rho.  The substring distances
+// come from the full code that verification loads anyway.  The rule depends
+// only on (query, code), so results do not depend on batching or order.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "index.h"
+#include "launch.h"
+#include "search.h"
+
+namespace mih {
+namespace {
+
+constexpr int kSearchThreads = 256;
+constexpr uint32_t kSliceEntries = 1024;   // big-bucket slice
+constexpr int kQueryShift = 41;            // composite entry: q << 41 | d << 32 | id
+constexpr uint64_t kEntryMask = (1ull << kQueryShift) - 1ull;
+
+struct BigSlice {
+    uint32_t q;
+    int32_t t;
+    uint32_t begin;
+    uint32_t end;
+};
+
+enum Mode { kModeKnn = 0, kModeCollect = 1, kModeCount = 2 };
+
+struct SearchArgs {
+    const TableDesc* tables;
+    int m, q;
+    const uint64_t* codes;
+    const uint64_t* queries;
+    uint32_t nq;
+    const int32_t* t_lo;               // per query first step of this launch
+    const int32_t* t_hi;               // per query last step (inclusive); < t_lo = idle
+    const uint64_t* chunk_off;         // [nq + 1]
+    unsigned long long* chunk_next;    // work counter
+    uint32_t* hist;                    // knn: [nq][q+1]
+    const int32_t* bound;              // knn: store if d <= bound; collect/count: keep if d <= bound
+    uint64_t* buf;                     // knn: [nq][cap]; collect: entries
+    uint32_t cap;                      // knn: slots per query
+    uint32_t* cnt;                     // knn: stored count; collect: cursor; count: count
+    const uint64_t* out_base;          // collect: first slot of each query, [nq + 1]
+    int* err;                          // collect: set if a query writes past its range
+    unsigned long long* qstats;        // [nq][4]: lookups, raw, unique, last step
+    BigSlice* big;
+    uint32_t big_cap;
+    unsigned int* big_count;
+    unsigned int* big_next;
+};
+
+// Chunks of step t for a query: ceil(C(s_j, rho) / 256), 0 if rho > s_j.
+__device__ __forceinline__ uint64_t step_chunks(const int* s_len, int m, int t) {
+    const int j = t % m, rho = t / m;
+    const uint64_t keys = binom(s_len[j], rho);
+    return (keys + kChunkKeys - 1) / kChunkKeys;
+}
+
+template <int W>
+__device__ __forceinline__ Code<W> load_query(const uint64_t* __restrict__ queries, uint32_t q) {
+    Code<W> g;
+#pragma unroll
+    for (int w = 0; w < W; ++w) g.w[w] = __ldg(queries + static_cast<uint64_t>(q) * W + w);
+    return g;
+}
+
+// Process one candidate per lane (valid lanes only), warp-synchronous: every
+// lane of the warp calls this together; all valid lanes share query q.
+template <int W, int MODE>
+__device__ __forceinline__ void handle_candidates(const SearchArgs& a, const int* s_off, const int* s_len,
+                                                  uint32_t q, int j, int rho, const Code<W>& g, bool valid,
+                                                  uint32_t id, uint32_t& unique_acc) {
+    int d = 0;
+    bool keep = false;
+    if (valid) {
+        const Code<W> c = load_code<W>(a.codes, id);
+        Code<W> x;
+#pragma unroll
+        for (int w = 0; w < W; ++w) x.w[w] = c.w[w] ^ g.w[w];
+#pragma unroll
+        for (int w = 0; w < W; ++w) d += __popcll(x.w[w]);
+        keep = true;
+        for (int jj = 0; jj < a.m; ++jj) {
+            if (jj == j) continue;
+            const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
+            if (jj < j ? (dj <= rho) : (dj < rho)) {
+                keep = false;
+                break;
+            }
+        }
+    }
+    const uint32_t lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+    if constexpr (MODE == kModeKnn) {
+        unique_acc += keep ? 1u : 0u;
+        // distance histogram, one atomic per distinct distance in the warp
+        const uint32_t hkey = keep ? static_cast<uint32_t>(d) : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, hkey);
+        if (keep && (peers & lt) == 0)
+            atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.q + 1) + d], static_cast<uint32_t>(__popc(peers)));
+        const bool store = keep && d <= __ldg(a.bound + q);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, store);
+        if (bal) {
+            uint32_t base = 0;
+            const int leader = __ffs(bal) - 1;
+            if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (store) {
+                const uint32_t p = base + __popc(bal & lt);
+                if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, id);
+            }
+        }
+    } else {
+        const bool take = keep && d <= __ldg(a.bound + q);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            uint32_t base = 0;
+            if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
+            if constexpr (MODE == kModeCollect) {
+                base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                if (take) {
+                    const uint64_t p = __ldg(a.out_base + q) + base + __popc(bal & lt);
+                    if (p < __ldg(a.out_base + q + 1)) a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(d, id);
+                    else atomicExch(a.err, 1);
+                }
+            }
+        }
+        if constexpr (MODE == kModeCount) unique_acc += keep ? 1u : 0u;
+        if constexpr (MODE == kModeCollect) unique_acc += keep ? 1u : 0u;
+    }
+}
+
+// Warp-cooperative pass over the union of up to 32 buckets [b, b + sz).
+template <int W, int MODE>
+__device__ __forceinline__ void scan_buckets(const SearchArgs& a, const int* s_off, const int* s_len,
+                                             const uint32_t* __restrict__ ids, uint32_t q, int j, int rho,
+                                             const Code<W>& g, uint32_t b, uint32_t sz, uint32_t& unique_acc) {
+    const uint32_t incl = warp_inclusive_scan(sz);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t excl = incl - sz;
+    const uint32_t lane = lane_id();
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t idx = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
+            if (e <= idx) owner += step;
+        }
+        const uint32_t ob = __shfl_sync(0xFFFFFFFFu, b, owner);
+        const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
+        const bool valid = idx < total;
+        const uint32_t id = valid ? __ldg(ids + ob + (idx - oe)) : 0u;
+        handle_candidates<W, MODE>(a, s_off, s_len, q, j, rho, g, valid, id, unique_acc);
+    }
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
+    __shared__ int s_off[kMaxTables];
+    __shared__ int s_len[kMaxTables];
+    for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
+        s_off[j] = a.tables[j].off;
+        s_len[j] = a.tables[j].len;
+    }
+    __syncthreads();
+    const uint32_t lane = lane_id();
+    const unsigned long long total_chunks = a.chunk_off[a.nq];
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(a.chunk_next, 1ull);
+        c = __shfl_sync(0xFFFFFFFFu, c, 0);
+        if (c >= total_chunks) break;
+        // query owning chunk c: last q with chunk_off[q] <= c
+        uint32_t lo = 0, hi = a.nq;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(a.chunk_off + mid) <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t q = lo;
+        uint64_t lc = c - __ldg(a.chunk_off + q);
+        int t = __ldg(a.t_lo + q);
+        for (;;) {
+            const uint64_t nch = step_chunks(s_len, a.m, t);
+            if (lc < nch) break;
+            lc -= nch;
+            ++t;
+        }
+        const int j = t % a.m, rho = t / a.m, s = s_len[j];
+        const uint64_t nkeys = binom(s, rho);
+        const uint64_t first = lc * kChunkKeys + static_cast<uint64_t>(lane) * kKeysPerLane;
+        const uint64_t left = first < nkeys ? nkeys - first : 0ull;
+        const int mine = left < static_cast<uint64_t>(kKeysPerLane) ? static_cast<int>(left) : kKeysPerLane;
+        const Code<W> g = load_query<W>(a.queries, q);
+        const uint32_t gkey = substring_bits<W>(g, s_off[j], s);
+        const TableDesc& tab = a.tables[j];
+        const uint32_t* ids = tab.ids;
+        uint64_t x = mine > 0 ? unrank_subset(first, s, rho) : 0ull;
+        uint32_t raw = 0, unique = 0;
+        for (int r = 0; r < kKeysPerLane; ++r) {
+            uint32_t b = 0, e = 0;
+            if (r < mine) {
+                lookup_bucket(tab, gkey ^ static_cast<uint32_t>(x), b, e);
+                if (rho > 0 && r + 1 < mine) x = next_subset(x);
+            }
+            uint32_t sz = e - b;
+            if (sz > kBigBucket) {
+                // Hand the bucket to the slice kernel; if the list is full the
+                // reserved slots are marked empty and the warp scans it here.
+                const uint32_t ns = (sz + kSliceEntries - 1) / kSliceEntries;
+                const unsigned int at = atomicAdd(a.big_count, ns);
+                const bool fits = static_cast<uint64_t>(at) + ns <= a.big_cap;
+                for (uint32_t i = 0; i < ns && at + i < a.big_cap; ++i) {
+                    BigSlice bs;
+                    bs.q = fits ? q : kPadId;
+                    bs.t = t;
+                    bs.begin = b + i * kSliceEntries;
+                    bs.end = min(e, bs.begin + kSliceEntries);
+                    a.big[at + i] = bs;
+                }
+                if (fits) {
+                    raw += sz;
+                    sz = 0;
+                }
+            }
+            raw += sz;
+            if (__any_sync(0xFFFFFFFFu, sz != 0))
+                scan_buckets<W, MODE>(a, s_off, s_len, ids, q, j, rho, g, b, sz, unique);
+        }
+        // per-query counters (lookups, raw candidates, unique candidates)
+        uint32_t lk = static_cast<uint32_t>(mine);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lk += __shfl_down_sync(0xFFFFFFFFu, lk, o);
+            raw += __shfl_down_sync(0xFFFFFFFFu, raw, o);
+            unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
+        }
+        if (lane == 0 && a.qstats) {
+            atomicAdd(&a.qstats[4ull * q + 0], static_cast<unsigned long long>(lk));
+            atomicAdd(&a.qstats[4ull * q + 1], static_cast<unsigned long long>(raw));
+            atomicAdd(&a.qstats[4ull * q + 2], static_cast<unsigned long long>(unique));
+        }
+    }
+}
+
+// Slices of large buckets, one warp per slice.
+template <int W, int MODE>
+__global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a) {
+    __shared__ int s_off[kMaxTables];
+    __shared__ int s_len[kMaxTables];
+    for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
+        s_off[j] = a.tables[j].off;
+        s_len[j] = a.tables[j].len;
+    }
+    __syncthreads();
+    const uint32_t lane = lane_id();
+    const unsigned int count = min(*a.big_count, a.big_cap);
+    for (;;) {
+        unsigned int i = 0;
+        if (lane == 0) i = atomicAdd(a.big_next, 1u);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        if (i >= count) break;
+        const BigSlice bs = a.big[i];
+        if (bs.q == kPadId) continue;
+        const int j = bs.t % a.m, rho = bs.t / a.m;
+        const Code<W> g = load_query<W>(a.queries, bs.q);
+        const uint32_t* ids = a.tables[j].ids;
+        uint32_t unique = 0;
+        for (uint32_t p = bs.begin; p < bs.end; p += 32) {
+            const bool valid = p + lane < bs.end;
+            const uint32_t id = valid ? __ldg(ids + p + lane) : 0u;
+            handle_candidates<W, MODE>(a, s_off, s_len, bs.q, j, rho, g, valid, id, unique);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
+        if (lane == 0 && a.qstats) atomicAdd(&a.qstats[4ull * bs.q + 2], static_cast<unsigned long long>(unique));
+    }
+}
+
+// ------------------------------------------------------------ planning
+// Chunk count of each query's step range [t_lo, t_hi].
+__global__ void plan_chunks_kernel(const TableDesc* __restrict__ tables, int m, uint32_t nq,
+                                   const int32_t* __restrict__ t_lo, const int32_t* __restrict__ t_hi,
+                                   uint64_t* __restrict__ chunks /* [nq + 1] */) {
+    __shared__ int s_len[kMaxTables];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
+    __syncthreads();
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x) {
+        uint64_t c = 0;
+        if (q < nq)
+            for (int t = t_lo[q]; t <= t_hi[q]; ++t) c += step_chunks(s_len, m, t);
+        chunks[q] = c;
+    }
+}
+
+__device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform, uint32_t q, uint64_t n) {
+    const uint64_t k = kq ? kq[q] : k_uniform;
+    return static_cast<uint32_t>(k < n ? k : n);
+}
+
+// Alg. 3 stopping test after step t_hi[q]; advances or retires each query.
+__global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32_t* __restrict__ kq,
+                                uint32_t k_uniform, const uint32_t* __restrict__ hist, int32_t* __restrict__ t_lo,
+                                int32_t* __restrict__ t_hi, int32_t* __restrict__ bound, int32_t* __restrict__ dk,
+                                unsigned long long* __restrict__ qstats, unsigned int* __restrict__ active) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int t = t_hi[q];
+        if (t < t_lo[q]) continue;  // retired earlier
+        const uint32_t kk = kk_of(kq, k_uniform, q, n);
+        const uint32_t* h = hist + static_cast<uint64_t>(q) * (qbits + 1);
+        uint64_t cum = 0;
+        int first_reach = -1;
+        for (int d = 0; d <= qbits; ++d) {
+            cum += h[d];
+            if (first_reach < 0 && cum >= kk) first_reach = d;
+        }
+        if (first_reach >= 0 && first_reach <= t) {
+            dk[q] = first_reach;            // all codes within t bits are known
+            t_lo[q] = t + 1;
+            qstats[4ull * q + 3] = static_cast<unsigned long long>(t);
+        } else {
+            t_lo[q] = t + 1;
+            t_hi[q] = t + 1;
+            bound[q] = first_reach >= 0 ? first_reach : qbits;  // upper bound on the k-th distance
+            atomicAdd(active, 1u);
+        }
+    }
+}
+
+// ------------------------------------------------------------ selection
+struct SelectArgs {
+    uint32_t nq;
+    uint64_t n;
+    int q;
+    const uint32_t* kq;
+    uint32_t k_uniform;
+    const uint64_t* out_off;
+    const uint32_t* hist;
+    const int32_t* dk;
+    const uint64_t* buf1;
+    uint32_t cap;
+    const uint32_t* cnt1;
+    const uint64_t* buf2;
+    const uint64_t* base2;
+    uint32_t* out_ids;
+    int32_t* out_dist;
+    int* err;
+};
+
+// Top-min(k, n) of one query: every entry closer than d_k, then the
+// (k - #closer) smallest ids at distance d_k (radix select on the id), sorted
+// by (distance, id) with a bitonic network in shared memory.
+__global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
+    extern __shared__ uint64_t res[];
+    __shared__ unsigned int s_n, s_hist[256];
+    __shared__ uint32_t s_prefix, s_remaining;
+    __shared__ unsigned long long s_below;
+    const uint32_t q = blockIdx.x;
+    const uint32_t k = a.kq ? a.kq[q] : a.k_uniform;
+    const uint64_t ob = a.out_off ? a.out_off[q] : static_cast<uint64_t>(q) * a.k_uniform;
+    const uint32_t kk = static_cast<uint32_t>(k < a.n ? k : a.n);
+    uint32_t* oid = a.out_ids + ob;
+    int32_t* odist = a.out_dist + ob;
+    if (kk == 0) {
+        for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) { oid[i] = kPadId; odist[i] = -1; }
+        return;
+    }
+    const int dk = a.dk[q];
+    const uint32_t* h = a.hist + static_cast<uint64_t>(q) * (a.q + 1);
+    if (threadIdx.x == 0) {
+        unsigned long long below = 0;
+        for (int d = 0; d < dk; ++d) below += h[d];
+        s_below = below;
+        s_n = 0;
+    }
+    __syncthreads();
+    const uint32_t ties = h[dk];
+    const uint32_t quota = kk - static_cast<uint32_t>(s_below);
+    const uint64_t* src;
+    uint64_t nsrc;
+    const uint32_t c1 = a.cnt1 ? a.cnt1[q] : 0xFFFFFFFFu;
+    if (a.cnt1 && c1 <= a.cap) {
+        src = a.buf1 + static_cast<uint64_t>(q) * a.cap;
+        nsrc = c1;
+    } else {
+        src = a.buf2 + a.base2[q];
+        nsrc = s_below + ties;
+    }
+    const bool take_all_ties = quota >= ties;
+    uint32_t P = 1;
+    while (P < kk) P <<= 1;
+    for (uint64_t i = threadIdx.x; i < nsrc; i += blockDim.x) {
+        const uint64_t e = src[i] & kEntryMask;
+        const int d = static_cast<int>(e >> 32);
+        if (d < dk || (d == dk && take_all_ties)) {
+            const unsigned int slot = atomicAdd(&s_n, 1u);
+            if (slot < P) res[slot] = e;
+        }
+    }
+    if (!take_all_ties) {
+        if (threadIdx.x == 0) { s_prefix = 0; s_remaining = quota; }
+        for (int pass = 3; pass >= 0; --pass) {
+            s_hist[threadIdx.x] = 0;
+            __syncthreads();
+            const int hi_shift = 8 * (pass + 1);
+            const uint32_t prefix = s_prefix;
+            for (uint64_t i = threadIdx.x; i < nsrc; i += blockDim.x) {
+                const uint64_t e = src[i] & kEntryMask;
+                if (static_cast<int>(e >> 32) != dk) continue;
+                const uint32_t id = static_cast<uint32_t>(e);
+                if (pass < 3 && (id >> hi_shift) != (prefix >> hi_shift)) continue;
+                atomicAdd(&s_hist[(id >> (8 * pass)) & 255u], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t rem = s_remaining, digit = 0;
+                for (; digit < 255; ++digit) {
+                    if (s_hist[digit] >= rem) break;
+                    rem -= s_hist[digit];
+                }
+                s_remaining = rem;
+                s_prefix = prefix | (digit << (8 * pass));
+            }
+            __syncthreads();
+        }
+        const uint32_t xid = s_prefix;  // the quota-th smallest tied id
+        for (uint64_t i = threadIdx.x; i < nsrc; i += blockDim.x) {
+            const uint64_t e = src[i] & kEntryMask;
+            if (static_cast<int>(e >> 32) == dk && static_cast<uint32_t>(e) <= xid) {
+                const unsigned int slot = atomicAdd(&s_n, 1u);
+                if (slot < P) res[slot] = e;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_n != kk) {
+        if (threadIdx.x == 0) atomicExch(a.err, 1);
+        return;
+    }
+    for (uint32_t i = kk + threadIdx.x; i < P; i += blockDim.x) res[i] = ~0ull;
+    __syncthreads();
+    for (uint32_t size = 2; size <= P; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                const uint32_t lo = 2 * i - (i & (stride - 1));
+                const uint32_t hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t x = res[lo], y = res[hi];
+                if ((x > y) == up) { res[lo] = y; res[hi] = x; }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+        if (i < kk) {
+            oid[i] = static_cast<uint32_t>(res[i]);
+            odist[i] = static_cast<int32_t>(res[i] >> 32);
+        } else {
+            oid[i] = kPadId;
+            odist[i] = -1;
+        }
+    }
+}
+
+// d_k and the buffer size of each overflowed query (second pass).
+__global__ void phase2_plan_kernel(uint32_t nq, int qbits, const uint32_t* __restrict__ hist,
+                                   const int32_t* __restrict__ dk, const uint32_t* __restrict__ cnt1, uint32_t cap,
+                                   int32_t* __restrict__ t_lo, int32_t* __restrict__ t_hi,
+                                   int32_t* __restrict__ bound, uint64_t* __restrict__ need,
+                                   unsigned int* __restrict__ n_over) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x) {
+        if (q == nq) { need[q] = 0; continue; }
+        const bool over = cnt1[q] > cap;
+        uint64_t c = 0;
+        if (over) {
+            const uint32_t* h = hist + static_cast<uint64_t>(q) * (qbits + 1);
+            for (int d = 0; d <= dk[q]; ++d) c += h[d];
+            atomicAdd(n_over, 1u);
+        }
+        need[q] = c;
+        t_lo[q] = 0;
+        t_hi[q] = over ? dk[q] : -1;
+        bound[q] = dk[q];
+    }
+}
+
+__global__ void init_knn_kernel(uint32_t nq, uint64_t n, int32_t* t_lo, int32_t* t_hi, int32_t* bound,
+                                int32_t* dk, int qbits) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        t_lo[q] = 0;
+        t_hi[q] = n > 0 ? 0 : -1;
+        bound[q] = qbits;
+        dk[q] = 0;
+    }
+}
+
+__global__ void init_range_kernel(uint32_t nq, int32_t lo, int32_t hi, int32_t bnd, int32_t* t_lo, int32_t* t_hi,
+                                  int32_t* bound) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        t_lo[q] = lo;
+        t_hi[q] = hi;
+        bound[q] = bnd;
+    }
+}
+
+__global__ void widen_counts_kernel(const uint32_t* __restrict__ cnt, uint32_t nq, uint64_t* __restrict__ out) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x)
+        out[q] = q < nq ? cnt[q] : 0ull;
+}
+
+__global__ void split_entries_kernel(const uint64_t* __restrict__ e, uint64_t total, uint32_t* __restrict__ ids,
+                                     int32_t* __restrict__ dist) {
+    for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint64_t v = e[i];
+        ids[i] = static_cast<uint32_t>(v);
+        dist[i] = static_cast<int32_t>((v >> 32) & 0x1FFu);
+    }
+}
+
+// Validation of per-query k: min, max and CSR consistency.
+__global__ void check_k_kernel(uint32_t nq, const uint32_t* __restrict__ kq, const uint64_t* __restrict__ off,
+                               unsigned int* __restrict__ out /* [min, max, bad] */) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t k = kq[q];
+        atomicMin(&out[0], k);
+        atomicMax(&out[1], k);
+        if (off && off[q + 1] - off[q] != k) atomicOr(&out[2], 1u);
+    }
+}
+
+unsigned grid1(uint64_t n) {
+    uint64_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    return static_cast<unsigned>(g ? g : 1);
+}
+
+template <int W, int MODE>
+mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s) {
+    static int bps = 0;  // resident blocks per SM (same on every GB300)
+    if (bps == 0) {
+        int v = 0;
+        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE>, kSearchThreads, 0));
+        bps = v > 0 ? v : 1;
+    }
+    search_kernel<W, MODE><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
+    MIH_LAUNCH_CHECK();
+    search_big_kernel<W, MODE><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
+template <int MODE>
+mih_status launch_search(const SearchArgs& a, int W, const DeviceInfo& dev, cudaStream_t s) {
+    if (W == 1) return launch_search_w<1, MODE>(a, dev, s);
+    if (W == 2) return launch_search_w<2, MODE>(a, dev, s);
+    return launch_search_w<4, MODE>(a, dev, s);
+}
+
+// Per-launch work state (chunk offsets, counters, big list).
+struct Plan {
+    uint64_t* chunk_off = nullptr;           // [nq + 1]
+    unsigned long long* counters = nullptr;  // [0] chunk_next; [1] big_count|big_next (as uint32 x2)
+    BigSlice* big = nullptr;
+    uint32_t big_cap = 0;
+};
+
+mih_status plan_alloc(Plan& p, uint32_t nq, Workspace& ws) {
+    MIH_TRY(ws.alloc(&p.chunk_off, static_cast<size_t>(nq) + 1));
+    MIH_TRY(ws.alloc(&p.counters, 2));
+    p.big_cap = 1u << 20;
+    MIH_TRY(ws.alloc(&p.big, p.big_cap));
+    return MIH_OK;
+}
+
+// Compute chunk offsets for the current step ranges and run one search launch.
+template <int MODE>
+mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
+                    const DeviceInfo& dev, Workspace& ws) {
+    cudaStream_t s = ws.stream();
+    plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, t_lo, t_hi, p.chunk_off);
+    MIH_LAUNCH_CHECK();
+    MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
+    MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
+    a.t_lo = t_lo;
+    a.t_hi = t_hi;
+    a.chunk_off = p.chunk_off;
+    a.chunk_next = p.counters;
+    a.big = p.big;
+    a.big_cap = p.big_cap;
+    a.big_count = reinterpret_cast<unsigned int*>(p.counters + 1);
+    a.big_next = a.big_count + 1;
+    return launch_search<MODE>(a, ix->W, dev, s);
+}
+
+mih_status check_flag(const int* err, const char* what, cudaStream_t s) {
+    int h = 0;
+    MIH_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        set_error("%s", what);
+        return MIH_EINTERNAL;
+    }
+    return MIH_OK;
+}
+
+mih_status validate_common(const mih_index* ix, const uint64_t* queries, uint32_t nq) {
+    if (!ix) {
+        set_error("index is NULL");
+        return MIH_EINVAL;
+    }
+    if (nq > (1u << 23)) {
+        set_error("nq must be at most 2^23");
+        return MIH_EINVAL;
+    }
+    int dev = 0;
+    MIH_CUDA(cudaGetDevice(&dev));
+    if (dev != ix->device) {
+        set_error("index was built on device %d, current device is %d", ix->device, dev);
+        return MIH_EINVAL;
+    }
+    if (nq > 0) MIH_TRY(check_device_ptr(queries, "queries"));
+    return MIH_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- exported
+// k validation shared with the linear scan: fills *kmax.
+mih_status check_k_args(uint32_t nq, const uint32_t* k, uint32_t k_uniform, const uint64_t* out_offsets,
+                        const uint32_t* out_ids, const int32_t* out_dist, uint32_t* kmax, Workspace& ws) {
+    if (nq == 0) {
+        *kmax = k ? 0 : k_uniform;
+        return MIH_OK;
+    }
+    MIH_TRY(check_device_ptr(out_ids, "out_ids"));
+    MIH_TRY(check_device_ptr(out_dist, "out_dist"));
+    if (!k) {
+        if (k_uniform < 1 || k_uniform > MIH_MAX_K) {
+            set_error("k must be in [1, %u] (got %u)", MIH_MAX_K, k_uniform);
+            return MIH_EINVAL;
+        }
+        if (out_offsets) {
+            set_error("out_offsets must be NULL when k is uniform");
+            return MIH_EINVAL;
+        }
+        *kmax = k_uniform;
+        return MIH_OK;
+    }
+    MIH_TRY(check_device_ptr(k, "k"));
+    MIH_TRY(check_device_ptr(out_offsets, "out_offsets"));
+    unsigned int* d;
+    MIH_TRY(ws.alloc(&d, 3));
+    unsigned int init[3] = {0xFFFFFFFFu, 0u, 0u};
+    MIH_CUDA(cudaMemcpyAsync(d, init, sizeof(init), cudaMemcpyHostToDevice, ws.stream()));
+    check_k_kernel<<<grid1(nq), 256, 0, ws.stream()>>>(nq, k, out_offsets, d);
+    MIH_LAUNCH_CHECK();
+    unsigned int h[3];
+    MIH_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, ws.stream()));
+    MIH_CUDA(cudaStreamSynchronize(ws.stream()));
+    if (h[0] < 1 || h[1] > MIH_MAX_K) {
+        set_error("every k must be in [1, %u] (min %u, max %u)", MIH_MAX_K, h[0], h[1]);
+        return MIH_EINVAL;
+    }
+    if (h[2]) {
+        set_error("out_offsets[i+1] - out_offsets[i] must equal k[i]");
+        return MIH_EINVAL;
+    }
+    *kmax = h[1];
+    return MIH_OK;
+}
+
+mih_status launch_select(const SelectInputs& in, Workspace& ws) {
+    if (in.nq == 0) return MIH_OK;
+    uint32_t P = 1;
+    const uint64_t kk_max = std::min<uint64_t>(in.kmax, in.n);
+    while (P < kk_max) P <<= 1;
+    const size_t smem = static_cast<size_t>(P) * sizeof(uint64_t);
+    if (smem > 48 * 1024) MIH_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        static_cast<int>(smem)));
+    int* err;
+    MIH_TRY(ws.alloc(&err, 1));
+    MIH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ws.stream()));
+    SelectArgs a;
+    a.nq = in.nq;
+    a.n = in.n;
+    a.q = in.q;
+    a.kq = in.kq;
+    a.k_uniform = in.k_uniform;
+    a.out_off = in.out_off;
+    a.hist = in.hist;
+    a.dk = in.dk;
+    a.buf1 = in.buf1;
+    a.cap = in.cap;
+    a.cnt1 = in.cnt1;
+    a.buf2 = in.buf2;
+    a.base2 = in.base2;
+    a.out_ids = in.out_ids;
+    a.out_dist = in.out_dist;
+    a.err = err;
+    select_kernel<<<in.nq, 256, smem, ws.stream()>>>(a);
+    MIH_LAUNCH_CHECK();
+    int herr = 0;
+    MIH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ws.stream()));
+    MIH_CUDA(cudaStreamSynchronize(ws.stream()));
+    if (herr) {
+        set_error("select: collected entry count differs from min(k, n)");
+        return MIH_EINTERNAL;
+    }
+    return MIH_OK;
+}
+
+uint32_t knn_buffer_cap(uint32_t kmax) {
+    uint64_t c = 8ull * kmax;
+    if (c < 1024) c = 1024;
+    if (c > 65536) c = 65536;
+    return static_cast<uint32_t>(c);
+}
+
+}  // namespace mih
+
+using namespace mih;
+
+extern "C" {
+
+mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, const uint32_t* k, uint32_t k_uniform,
+                   const uint64_t* out_offsets, uint32_t* out_ids, int32_t* out_dist, uint64_t* query_stats,
+                   mih_stats* stats, void* stream) {
+    clear_error();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    MIH_TRY(validate_common(ix, queries, nq));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    uint32_t kmax = 0;
+    MIH_TRY(check_k_args(nq, k, k_uniform, out_offsets, out_ids, out_dist, &kmax, ws));
+    if (query_stats) MIH_TRY(check_device_ptr(query_stats, "query_stats"));
+    if (nq == 0) return MIH_OK;
+    DeviceInfo dev;
+    MIH_TRY(device_info(&dev));
+    const int qb = ix->q;
+    const uint32_t cap = knn_buffer_cap(kmax);
+
+    int32_t *t_lo, *t_hi, *bound, *dk;
+    uint32_t *hist, *cnt1;
+    uint64_t* buf1;
+    unsigned long long* qstats;
+    unsigned int* active;
+    MIH_TRY(ws.alloc(&t_lo, nq));
+    MIH_TRY(ws.alloc(&t_hi, nq));
+    MIH_TRY(ws.alloc(&bound, nq));
+    MIH_TRY(ws.alloc(&dk, nq));
+    MIH_TRY(ws.alloc(&hist, static_cast<size_t>(nq) * (qb + 1)));
+    MIH_TRY(ws.alloc(&cnt1, nq));
+    MIH_TRY(ws.alloc(&buf1, static_cast<size_t>(nq) * cap));
+    MIH_TRY(ws.alloc(&qstats, 4ull * nq));
+    MIH_TRY(ws.alloc(&active, 1));
+    MIH_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nq * (qb + 1), s));
+    MIH_CUDA(cudaMemsetAsync(cnt1, 0, sizeof(uint32_t) * nq, s));
+    MIH_CUDA(cudaMemsetAsync(qstats, 0, sizeof(unsigned long long) * 4 * nq, s));
+    init_knn_kernel<<<grid1(nq), 256, 0, s>>>(nq, ix->n, t_lo, t_hi, bound, dk, qb);
+    MIH_LAUNCH_CHECK();
+    Plan plan;
+    MIH_TRY(plan_alloc(plan, nq, ws));
+
+    SearchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tables = ix->dev_tables;
+    a.m = ix->m;
+    a.q = qb;
+    a.codes = ix->codes;
+    a.queries = queries;
+    a.nq = nq;
+    a.hist = hist;
+    a.bound = bound;
+    a.buf = buf1;
+    a.cap = cap;
+    a.cnt = cnt1;
+    a.qstats = qstats;
+
+    uint64_t waves = 0;
+    if (ix->n > 0) {
+        for (int t = 0; t <= qb; ++t) {
+            MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws));
+            ++waves;
+            MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), s));
+            knn_stop_kernel<<<grid1(nq), 256, 0, s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
+                                                     qstats, active);
+            MIH_LAUNCH_CHECK();
+            unsigned int hact = 0;
+            MIH_CUDA(cudaMemcpyAsync(&hact, active, sizeof(hact), cudaMemcpyDeviceToHost, s));
+            MIH_CUDA(cudaStreamSynchronize(s));
+            if (hact == 0) break;
+            if (t == qb) {
+                set_error("mih_knn: queries still active after q steps");
+                return MIH_EINTERNAL;
+            }
+        }
+    }
+
+    // Second pass for queries whose bounded buffer overflowed.
+    uint64_t* need;
+    unsigned int* n_over;
+    MIH_TRY(ws.alloc(&need, static_cast<size_t>(nq) + 1));
+    MIH_TRY(ws.alloc(&n_over, 1));
+    MIH_CUDA(cudaMemsetAsync(n_over, 0, sizeof(unsigned int), s));
+    phase2_plan_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, qb, hist, dk, cnt1, cap, t_lo, t_hi, bound, need, n_over);
+    MIH_LAUNCH_CHECK();
+    unsigned int hover = 0;
+    MIH_CUDA(cudaMemcpyAsync(&hover, n_over, sizeof(hover), cudaMemcpyDeviceToHost, s));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    uint64_t* buf2 = nullptr;
+    if (hover > 0 && ix->n > 0) {
+        MIH_TRY(scan_exclusive_u64(need, need, static_cast<size_t>(nq) + 1, ws));
+        uint64_t total = 0;
+        MIH_CUDA(cudaMemcpyAsync(&total, need + nq, sizeof(total), cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        MIH_TRY(ws.alloc(&buf2, total));
+        uint32_t* cursor;
+        MIH_TRY(ws.alloc(&cursor, nq));
+        MIH_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, s));
+        int* err;
+        MIH_TRY(ws.alloc(&err, 1));
+        MIH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        SearchArgs b = a;
+        b.buf = buf2;
+        b.cnt = cursor;
+        b.out_base = need;
+        b.qstats = nullptr;
+        b.err = err;
+        MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
+        ++waves;
+        MIH_TRY(check_flag(err, "mih_knn: second pass found more codes within d_k than counted", s));
+    }
+
+    SelectInputs si;
+    si.nq = nq;
+    si.n = ix->n;
+    si.q = qb;
+    si.kq = k;
+    si.k_uniform = k_uniform;
+    si.kmax = kmax;
+    si.out_off = out_offsets;
+    si.hist = hist;
+    si.dk = dk;
+    si.buf1 = buf1;
+    si.cap = cap;
+    si.cnt1 = cnt1;
+    si.buf2 = buf2;
+    si.base2 = need;
+    si.out_ids = out_ids;
+    si.out_dist = out_dist;
+    MIH_TRY(launch_select(si, ws));
+
+    if (query_stats)
+        MIH_CUDA(cudaMemcpyAsync(query_stats, qstats, sizeof(uint64_t) * 4 * nq, cudaMemcpyDeviceToDevice, s));
+    if (stats) {
+        std::vector<unsigned long long> h(4ull * nq);
+        MIH_CUDA(cudaMemcpyAsync(h.data(), qstats, sizeof(unsigned long long) * 4 * nq, cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        for (uint32_t i = 0; i < nq; ++i) {
+            stats->lookups += h[4ull * i];
+            stats->candidates_raw += h[4ull * i + 1];
+            stats->candidates_unique += h[4ull * i + 2];
+            stats->steps += ix->n > 0 ? h[4ull * i + 3] + 1 : 0;
+        }
+        stats->phase2_queries = hover;
+        stats->waves = waves;
+    }
+    MIH_CUDA(cudaStreamSynchronize(s));
+    return MIH_OK;
+}
+
+mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, int r, uint64_t capacity,
+                     uint64_t* out_offsets, uint32_t* out_ids, int32_t* out_dist, uint64_t* total_out,
+                     uint64_t* query_stats, mih_stats* stats, void* stream) {
+    clear_error();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (total_out) *total_out = 0;
+    MIH_TRY(validate_common(ix, queries, nq));
+    if (r < 0) {
+        set_error("mih_rnear: r must be >= 0");
+        return MIH_EINVAL;
+    }
+    MIH_TRY(check_device_ptr(out_offsets, "out_offsets"));
+    if (capacity > 0) {
+        MIH_TRY(check_device_ptr(out_ids, "out_ids"));
+        MIH_TRY(check_device_ptr(out_dist, "out_dist"));
+    }
+    if (query_stats) MIH_TRY(check_device_ptr(query_stats, "query_stats"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    DeviceInfo dev;
+    MIH_TRY(device_info(&dev));
+    const int qb = ix->q;
+    const int reff = r < qb ? r : qb;  // every code lies within q bits
+    int32_t *t_lo, *t_hi, *bound;
+    uint32_t* cnt;
+    unsigned long long* qstats;
+    const uint32_t nqa = nq > 0 ? nq : 1;
+    MIH_TRY(ws.alloc(&t_lo, nqa));
+    MIH_TRY(ws.alloc(&t_hi, nqa));
+    MIH_TRY(ws.alloc(&bound, nqa));
+    MIH_TRY(ws.alloc(&cnt, nqa));
+    MIH_TRY(ws.alloc(&qstats, 4ull * nqa));
+    MIH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nqa, s));
+    MIH_CUDA(cudaMemsetAsync(qstats, 0, sizeof(unsigned long long) * 4 * nqa, s));
+    Plan plan;
+    MIH_TRY(plan_alloc(plan, nqa, ws));
+    SearchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tables = ix->dev_tables;
+    a.m = ix->m;
+    a.q = qb;
+    a.codes = ix->codes;
+    a.queries = queries;
+    a.nq = nq;
+    a.bound = bound;
+    a.cnt = cnt;
+    a.qstats = qstats;
+    if (nq > 0 && ix->n > 0) {
+        init_range_kernel<<<grid1(nq), 256, 0, s>>>(nq, 0, reff, reff, t_lo, t_hi, bound);
+        MIH_LAUNCH_CHECK();
+        MIH_TRY(run_wave<kModeCount>(ix, a, plan, t_lo, t_hi, dev, ws));
+    }
+    // CSR offsets of the results: exclusive scan of the counts, last = total
+    uint64_t* off64;
+    MIH_TRY(ws.alloc(&off64, static_cast<size_t>(nq) + 1));
+    widen_counts_kernel<<<grid1(nq + 1), 256, 0, s>>>(cnt, nq, off64);
+    MIH_LAUNCH_CHECK();
+    MIH_TRY(scan_exclusive_u64(off64, off64, static_cast<size_t>(nq) + 1, ws));
+    MIH_CUDA(cudaMemcpyAsync(out_offsets, off64, sizeof(uint64_t) * (nq + 1), cudaMemcpyDeviceToDevice, s));
+    uint64_t total = 0;
+    MIH_CUDA(cudaMemcpyAsync(&total, off64 + nq, sizeof(total), cudaMemcpyDeviceToHost, s));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    if (total_out) *total_out = total;
+    auto finish_stats = [&]() -> mih_status {
+        if (nq == 0) return MIH_OK;
+        std::vector<unsigned long long> h(4ull * nq);
+        MIH_CUDA(cudaMemcpyAsync(h.data(), qstats, sizeof(unsigned long long) * 4 * nq, cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        for (uint32_t i = 0; i < nq; ++i) h[4ull * i + 3] = static_cast<unsigned long long>(reff);
+        if (query_stats)
+            MIH_CUDA(cudaMemcpyAsync(query_stats, h.data(), sizeof(uint64_t) * 4 * nq, cudaMemcpyHostToDevice, s));
+        if (stats) {
+            for (uint32_t i = 0; i < nq; ++i) {
+                stats->lookups += h[4ull * i];
+                stats->candidates_raw += h[4ull * i + 1];
+                stats->candidates_unique += h[4ull * i + 2];
+                stats->steps += ix->n > 0 ? static_cast<uint64_t>(reff) + 1 : 0;
+            }
+            stats->waves = ix->n > 0 ? 1 : 0;
+        }
+        MIH_CUDA(cudaStreamSynchronize(s));
+        return MIH_OK;
+    };
+    if (total > capacity) {
+        MIH_TRY(finish_stats());
+        set_error("mih_rnear: %llu results exceed capacity %llu", static_cast<unsigned long long>(total),
+                  static_cast<unsigned long long>(capacity));
+        return MIH_EOVERFLOW;
+    }
+    if (total >= 0xFFFFFFFFull) {
+        set_error("mih_rnear: more than 2^32 - 2 results in one call");
+        return MIH_EINVAL;
+    }
+    if (total > 0) {
+        uint64_t *ent, *ent_alt, *sorted;
+        MIH_TRY(ws.alloc(&ent, total));
+        MIH_TRY(ws.alloc(&ent_alt, total));
+        MIH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nq, s));
+        int* err;
+        MIH_TRY(ws.alloc(&err, 1));
+        MIH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        SearchArgs b = a;
+        b.buf = ent;
+        b.out_base = off64;
+        b.qstats = nullptr;
+        b.err = err;
+        MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
+        MIH_TRY(check_flag(err, "mih_rnear: fill pass found more results than the count pass", s));
+        int qbits = 1;
+        while ((1u << qbits) < nq) ++qbits;
+        MIH_TRY(radix_sort_keys_u64(ent, ent_alt, total, kQueryShift + qbits, ws, &sorted));
+        split_entries_kernel<<<grid1(total), 256, 0, s>>>(sorted, total, out_ids, out_dist);
+        MIH_LAUNCH_CHECK();
+    }
+    MIH_TRY(finish_stats());
+    MIH_CUDA(cudaStreamSynchronize(s));
+    return MIH_OK;
+}
+
+}  // extern "C"

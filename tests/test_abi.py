@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads and exports every symbol include/mih.h
+declares; host-only helpers (no GPU) behave as the paper states."""
+import os
+import re
+import subprocess
+from math import log2
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mih.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1307_2982_gb300 as mih
+
+    mih.build()
+    mih.load()
+    return mih
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"MIH_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)))
+
+
+def test_header_declares_expected(lib):
+    names = declared_functions()
+    assert set(names) == set(lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    # only the C-ABI is visible
+    ours = {e for e in exported if e.startswith(("mih_", "linscan_"))}
+    assert ours == set(declared_functions())
+
+
+def test_build_targets_sm103a_only(lib):
+    from paper_1307_2982_gb300 import build_ext
+
+    assert build_ext.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings_and_version(lib):
+    assert lib.mih_status_str(0) == "MIH_OK"
+    for s in range(1, 7):
+        assert lib.mih_status_str(s).startswith("MIH_E")
+    assert "sm_103a" in lib.mih_version()
+
+
+def test_layout_matches_oracle(lib, orc):
+    for q in (64, 128, 256):
+        for m in range(1, q + 1):
+            off, ln = lib.mih_substring_layout(q, m)
+            o2, l2 = orc.substring_layout(q, m)
+            assert off == list(o2) and ln == list(l2)
+    with pytest.raises(lib.MihError):
+        lib.mih_substring_layout(64, 65)
+    with pytest.raises(lib.MihError):
+        lib.mih_substring_layout(64, 0)
+
+
+def test_cost_model_eq7(lib):
+    from math import comb
+
+    for q, n, s, r in [(64, 10**6, 16, 10), (128, 10**9, 32, 12), (256, 10**9, 32, 40), (240, 10**9, 30, 20)]:
+        want = (1 + n / 2**s) * (q / s) * sum(comb(s, z) for z in range((s * r) // q + 1))   # Eq. 7
+        assert lib.mih_cost_model(q, n, s, r) == pytest.approx(want, rel=1e-12)
+    assert lib.mih_cost_model(64, 10, 0, 3) < 0
+
+
+def test_suggest_m_table4(lib):
+    """Table 4: the selected m is usually the integer closest to q / log2(n)."""
+    from test_oracle_pins import golden
+
+    for q, n, v in golden("table4_q_over_log2n"):
+        m = lib.mih_suggest_m(q, n)
+        assert m == max(round(q / log2(n)), -(-q // 32))
+    # Table 4's selected values at n = 1e9 with substrings capped at 32 bits
+    assert lib.mih_suggest_m(64, 10**9) == 2
+    assert lib.mih_suggest_m(128, 10**9) == 4
+    assert lib.mih_suggest_m(256, 10**9) == 9   # 8.56 rounds to 9; the paper's CV picked 8

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Everything here is integer work, so the bar is bit-exact: ids and distances
+in (distance, id) order must equal the oracle's element by element.  The
+MIH work counters (lookups, raw and unique candidates, last step) must equal
+the oracle's step-by-step run of Algorithm 3.
+"""
+import numpy as np
+import pytest
+
+from paper_1307_2982_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def to_dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def ids_of(t):
+    return host(t).view(np.uint32)
+
+
+def tie_heavy(n, q, seed, pool=40):
+    p = synth.uniform_codes(pool, q, seed + 100)
+    return p[np.random.default_rng(seed).integers(0, pool, n)]
+
+
+def perturb(codes, flips, seed):
+    rng = np.random.default_rng(seed)
+    by = np.ascontiguousarray(codes).view(np.uint8).reshape(len(codes), -1)
+    bits = np.unpackbits(by, axis=1, bitorder="little")
+    for i in range(len(bits)):
+        bits[i, rng.choice(bits.shape[1], size=flips, replace=False)] ^= 1
+    return np.packbits(bits, axis=1, bitorder="little").view(np.uint64).reshape(len(codes), -1)
+
+
+def workload(kind, q, n, nq, seed=0):
+    if kind == "uniform":
+        return synth.uniform_codes(n, q, seed), synth.uniform_codes(nq, q, seed + 1)
+    if kind == "lsh":
+        return synth.lsh_codes(n, q, seed), synth.lsh_codes(nq, q, seed + 1)
+    db = tie_heavy(n, q, seed)
+    return db, perturb(db[:nq], 3, seed + 2)
+
+
+# (kind, q, n, nq, m list) -- sizes span many chunks/tiles with ragged tails
+KNN_CASES = [
+    ("uniform", 64, 100_000, 300, [4, 3, 2]),
+    ("lsh", 128, 200_003, 257, [6, 4, 5]),
+    ("lsh", 256, 60_001, 130, [9, 8, 12]),
+    ("ties", 128, 30_000, 100, [4, 6]),
+]
+
+
+@pytest.mark.parametrize("kind,q,n,nq,ms", KNN_CASES)
+def test_linscan_and_mih_knn_match_oracle(gpu_lib, orc, kind, q, n, nq, ms):
+    mih = gpu_lib
+    db, qs = workload(kind, q, n, nq)
+    codes, queries = to_dev(db), to_dev(qs)
+    indexes = {m: mih.mih_build(codes, q, m) for m in ms}
+    for k in (1, 10, 100):
+        want_ids, want_dist = orc.knn(db, qs, k)
+        ls = mih.linscan_knn(codes, q, queries, k)
+        assert np.array_equal(ids_of(ls["ids"]), want_ids), ("linscan ids", k)
+        assert np.array_equal(host(ls["dist"]), want_dist), ("linscan dist", k)
+        for m, ix in indexes.items():
+            r = mih.mih_knn(ix, queries, k)
+            assert np.array_equal(ids_of(r["ids"]), want_ids), ("mih ids", m, k)
+            assert np.array_equal(host(r["dist"]), want_dist), ("mih dist", m, k)
+    for ix in indexes.values():
+        ix.free()
+
+
+@pytest.mark.parametrize("table_kind", [1, 2])
+def test_table_kinds_agree(gpu_lib, orc, table_kind):
+    """Direct and sparse tables (Sec. 6) give the same answers."""
+    mih = gpu_lib
+    db, qs = workload("lsh", 128, 50_000, 64, seed=5)
+    codes, queries = to_dev(db), to_dev(qs)
+    ix = mih.mih_build(codes, 128, 6, table_kind=table_kind)
+    info = ix.info()
+    assert set(info["table_kind"]) == {table_kind}
+    assert sum(info["distinct_keys"]) > 0
+    want_ids, want_dist = orc.knn(db, qs, 50)
+    r = mih.mih_knn(ix, queries, 50)
+    assert np.array_equal(ids_of(r["ids"]), want_ids)
+    assert np.array_equal(host(r["dist"]), want_dist)
+
+
+@pytest.mark.parametrize("kind,q,m,n", [("uniform", 64, 4, 20_000), ("lsh", 128, 6, 20_000),
+                                        ("ties", 64, 3, 5_000), ("lsh", 256, 9, 8_000)])
+def test_mih_work_counters_match_alg3(gpu_lib, orc, kind, q, m, n):
+    """Per-query lookups, raw/unique candidates and last step equal Alg. 3 on the CPU."""
+    mih = gpu_lib
+    db, qs = workload(kind, q, n, 24, seed=9)
+    mo = orc.MihOracle(db, q, m)
+    ix = mih.mih_build(to_dev(db), q, m)
+    for k in (1, 25):
+        r = mih.mih_knn(ix, to_dev(qs), k, query_stats=True)
+        st = host(r["query_stats"])
+        for i in range(len(qs)):
+            ids, dist, cnt = mo.knn(qs[i], k)
+            assert np.array_equal(ids_of(r["ids"])[i], ids) and np.array_equal(host(r["dist"])[i], dist)
+            assert tuple(st[i]) == tuple(cnt), (i, k, st[i], cnt)
+
+
+def test_per_query_k_and_padding(gpu_lib, orc):
+    mih = gpu_lib
+    import torch
+
+    q, n, nq = 64, 3000, 200
+    db, qs = workload("uniform", q, n, nq, seed=13)
+    ks = synth.per_query_k(nq, seed=3, kmax=4000)          # some k > n: padded
+    codes, queries = to_dev(db), to_dev(qs)
+    off, want_ids, want_dist = orc.knn(db, qs, ks)
+    kt = torch.from_numpy(ks.astype(np.int32)).cuda()
+    ix = mih.mih_build(codes, q, 3)
+    for r in (mih.mih_knn(ix, queries, kt), mih.linscan_knn(codes, q, queries, kt)):
+        assert np.array_equal(host(r["offsets"]), off.astype(np.int64))
+        assert np.array_equal(ids_of(r["ids"]), want_ids)
+        assert np.array_equal(host(r["dist"]), want_dist)
+
+
+@pytest.mark.parametrize("q,m", [(64, 4), (128, 4), (256, 8)])
+def test_rnear_matches_oracle(gpu_lib, orc, q, m):
+    mih = gpu_lib
+    db, qs = workload("lsh", q, 40_000, 50, seed=21)
+    codes, queries = to_dev(db), to_dev(qs)
+    ix = mih.mih_build(codes, q, m)
+    for r in (0, 3, 9, q // 8, q // 4, q, q + 7):
+        woff, wid, wd = orc.rnear(db, qs, r)
+        if int(woff[-1]) > 3_000_000:
+            continue
+        got = mih.mih_rnear(ix, queries, r)
+        assert np.array_equal(host(got["offsets"]), woff.astype(np.int64)), r
+        assert np.array_equal(ids_of(got["ids"]), wid), r
+        assert np.array_equal(host(got["dist"]), wd), r
+
+
+def test_rnear_overflow_protocol(gpu_lib, orc):
+    mih = gpu_lib
+    import ctypes
+
+    import torch
+
+    q = 64
+    db, qs = workload("uniform", q, 10_000, 20, seed=3)
+    codes, queries = to_dev(db), to_dev(qs)
+    ix = mih.mih_build(codes, q, 4)
+    woff, wid, wd = orc.rnear(db, qs, 20)
+    assert woff[-1] > 5
+    off = torch.empty(21, dtype=torch.int64, device="cuda")
+    ids = torch.empty(5, dtype=torch.int32, device="cuda")
+    dist = torch.empty(5, dtype=torch.int32, device="cuda")
+    total = ctypes.c_uint64(0)
+    lib = mih.load()
+    s = lib.mih_rnear(ix.handle, mih._ptr(queries), 20, 20, 5, mih._ptr(off), mih._ptr(ids), mih._ptr(dist),
+                      ctypes.byref(total), None, None, mih._stream(None))
+    assert s == mih.MIH_EOVERFLOW
+    assert total.value == woff[-1]
+    assert np.array_equal(host(off), woff.astype(np.int64))
+
+
+def test_schedule_invariance(gpu_lib, orc):
+    """A query alone and inside a batch gives the same bytes (any m)."""
+    mih = gpu_lib
+    db, qs = workload("lsh", 128, 100_000, 500, seed=31)
+    codes, queries = to_dev(db), to_dev(qs)
+    ixs = [mih.mih_build(codes, 128, m) for m in (4, 6)]
+    batch = [mih.mih_knn(ix, queries, 30) for ix in ixs]
+    for i in (0, 17, 499):
+        single = mih.mih_knn(ixs[0], queries[i:i + 1], 30)
+        for b in batch:
+            assert np.array_equal(ids_of(single["ids"])[0], ids_of(b["ids"])[i])
+            assert np.array_equal(host(single["dist"])[0], host(b["dist"])[i])
+
+
+def test_edge_cases(gpu_lib, orc):
+    mih = gpu_lib
+    import torch
+
+    q = 128
+    db, qs = workload("uniform", q, 1000, 5, seed=41)
+    codes, queries = to_dev(db), to_dev(qs)
+    ix = mih.mih_build(codes, q, 4)
+    # empty query batch
+    r = mih.mih_knn(ix, queries[:0], 5)
+    assert r["ids"].shape == (0, 5)
+    # k at its maximum (> n): all n codes then padding
+    want_ids, want_dist = orc.knn(db, qs, mih.MIH_MAX_K)
+    for r in (mih.mih_knn(ix, queries, mih.MIH_MAX_K), mih.linscan_knn(codes, q, queries, mih.MIH_MAX_K)):
+        assert np.array_equal(ids_of(r["ids"]), want_ids)
+        assert np.array_equal(host(r["dist"]), want_dist)
+    # one-code database, and an empty database
+    one = mih.mih_build(codes[:1], q, 4)
+    w1, d1 = orc.knn(db[:1], qs, 3)
+    r = mih.mih_knn(one, queries, 3)
+    assert np.array_equal(ids_of(r["ids"]), w1) and np.array_equal(host(r["dist"]), d1)
+    empty = mih.mih_build(codes[:0], q, 4)
+    r = mih.mih_knn(empty, queries, 3)
+    assert np.all(ids_of(r["ids"]) == 0xFFFFFFFF) and np.all(host(r["dist"]) == -1)
+    r = mih.linscan_knn(codes[:0], q, queries, 3)
+    assert np.all(host(r["dist"]) == -1)
+    # all-equal database: ties broken by id
+    same = to_dev(np.repeat(db[:1], 5000, axis=0))
+    ixs = mih.mih_build(same, q, 4)
+    for r in (mih.mih_knn(ixs, queries[:2], 100), mih.linscan_knn(same, q, queries[:2], 100)):
+        assert np.array_equal(ids_of(r["ids"])[0], np.arange(100, dtype=np.uint32))
+    # invalid arguments are rejected with MIH_EINVAL
+    for bad in (lambda: mih.mih_knn(ix, queries, 0), lambda: mih.mih_knn(ix, queries, mih.MIH_MAX_K + 1),
+                lambda: mih.mih_build(codes, q, 3), lambda: mih.mih_build(codes, q, 129),
+                lambda: mih.mih_rnear(ix, queries, -1)):
+        with pytest.raises(mih.MihError) as e:
+            bad()
+        assert e.value.status == mih.MIH_EINVAL
+    # host memory is refused, not dereferenced
+    lib = mih.load()
+    import ctypes
+
+    h = ctypes.c_void_p()
+    hostbuf = torch.zeros((10, 2), dtype=torch.int64)
+    assert lib.mih_build(mih._ptr(hostbuf), 10, 128, 4, None, None, ctypes.byref(h)) == mih.MIH_EINVAL
