@@ -1,0 +1,429 @@
+"""Benchmark: exact 100-NN queries/s on 1B x 128-bit codes, multi-index
+hashing vs linear scan, on GB300.
+
+A step is one batch of 10,000 queries through mih_knn (Algorithm 3) on an
+index built once over n = 10^9 LSH-style 128-bit codes (m = 4 substrings of
+32 bits).  Inputs are resident in HBM when the timed region starts; the
+codes (16 GB) and the tables are far larger than L2, so no flush is needed.
+The same batch through linscan_knn is timed once as the comparator, the
+end-to-end figure adds the host<->device copies through the C-ABI, and the
+CPU oracle is timed on a bounded sample of queries (the reported baseline).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload H|1|2|3|4] [--n N] [--nq NQ] [--k K] [--m M]
+
+Multi-GPU: one process per GPU (torchrun), every rank holds the whole
+database (replicas) and answers its own 10,000 queries; value = all queries
+of all ranks / the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "exact 100-NN queries/s on 1B×128-bit codes, MIH vs linear scan on GB300; p99 ms"
+
+# workload name -> (kind, n, q, nq, k, m); "kper" = per-query log-uniform k
+WORKLOADS = {
+    "H": ("lsh", 1_000_000_000, 128, 10_000, 100, 4),
+    "1": ("uniform", 100_000, 64, 1_000, 100, 4),
+    "2": ("lsh", 10_000_000, 128, 10_000, 100, 6),
+    "3": ("uniform", 1_000_000_000, 64, 10_000, "kper", 2),
+    "4": ("lsh", 1_000_000_000, 256, 10_000, "kper", 9),
+}
+WORKLOAD_NAMES = {
+    "H": "1B x 128-bit LSH-style codes, 10k queries, k=100",
+    "1": "100k x 64-bit uniform codes, 1k queries, k=100",
+    "2": "10M x 128-bit LSH-style codes, 10k queries, k=100",
+    "3": "1B x 64-bit uniform codes, 10k queries, k log-uniform [1,1000]",
+    "4": "1B x 256-bit LSH-style codes, 10k queries, k log-uniform [1,1000]",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="H", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--nq", type=int, default=None)
+    ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--cpu-sample", type=int, default=32, help="queries timed on the CPU oracle")
+    ap.add_argument("--no-linscan", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    return a
+
+
+def workload(a):
+    kind, n, q, nq, k, m = WORKLOADS[a.workload]
+    n = a.n or n
+    nq = a.nq or nq
+    k = a.k or k
+    m = a.m or m
+    return kind, n, q, nq, k, m
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_codes(kind, n, q, seed, device):
+    from paper_1307_2982_gb300 import synth
+
+    if kind == "uniform":
+        return synth.uniform_codes_torch(n, q, seed, device=device)
+    return synth.lsh_codes_torch(n, q, seed, device=device)
+
+
+def per_query_k(nq, k, seed_shift=0):
+    from paper_1307_2982_gb300 import synth
+
+    if k == "kper":
+        return synth.per_query_k(nq, seed=3 + seed_shift, kmax=1000)
+    return None
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_oracle_time(db_host, qs_host, k, sample: int):
+    """Time the oracle on `sample` queries with all host cores; (q/s, cores, results)."""
+    import oracle
+
+    oracle.build()
+    qs = np.ascontiguousarray(qs_host[:sample])
+    cores = min(oracle.default_threads(), len(qs))
+    t0 = time.perf_counter()
+    res = oracle.knn(db_host, qs, k if isinstance(k, int) else k[:sample], nthreads=cores)
+    dt = time.perf_counter() - t0
+    return len(qs) / dt, cores, dt, res
+
+
+# ------------------------------------------------------------------- arms
+def run_reference(a):
+    """The oracle (plain CPU linear scan) on a bounded sample of the same workload."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+
+    kind, n, q, nq, k, m = workload(a)
+    dev = torch.device("cuda", local) if torch.cuda.is_available() else torch.device("cpu")
+    codes = make_codes(kind, n, q, 0, dev)
+    queries = make_codes(kind, nq, q, 1, dev)
+    db = codes.cpu().numpy().view(np.uint64)
+    qs = queries.cpu().numpy().view(np.uint64)
+    del codes, queries
+    kq = per_query_k(nq, k)
+    kk = k if kq is None else kq
+    oracle.build()
+    cores = oracle.default_threads()
+    # per step: a bounded sample sized for a few seconds of CPU work
+    sample = max(1, min(a.cpu_sample, nq))
+    for _ in range(a.warmup):
+        oracle.knn(db, qs[:min(sample, cores)], kk if isinstance(kk, int) else kk[:min(sample, cores)],
+                   nthreads=cores)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(a.steps):
+        lo = (s * sample) % nq
+        sl = slice(lo, min(nq, lo + sample))
+        oracle.knn(db, qs[sl], kk if isinstance(kk, int) else kk[sl], nthreads=cores)
+        done += sl.stop - sl.start
+    dt = time.perf_counter() - t0
+    value = done / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[a.workload], "n": n, "q": q, "nq": nq, "k": k if k != "kper" else
+                   "log-uniform[1,1000]", "codes": kind},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} queries per step over all {n} codes"},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import torch
+
+    import paper_1307_2982_gb300 as mih
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    mih.load()
+    kind, n, q, nq, k, m = workload(a)
+    W = q // 64
+
+    # inputs: the whole database on every rank, this rank's own queries
+    t0 = time.perf_counter()
+    codes = make_codes(kind, n, q, 0, dev)
+    all_q = make_codes(kind, nq * world, q, 1, dev)
+    queries = all_q[rank * nq:(rank + 1) * nq].contiguous()
+    del all_q
+    kq_np = per_query_k(nq, k, seed_shift=rank)
+    kt = torch.from_numpy(kq_np.astype(np.int32)).to(dev) if kq_np is not None else None
+    karg = kt if kt is not None else k
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    # index build (Algorithm 1), timed on the device
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    index = mih.mih_build(codes, q, m)
+    ev1.record()
+    torch.cuda.synchronize()
+    build_ms = ev0.elapsed_time(ev1)
+    info = index.info()
+
+    # outputs preallocated (the call writes into caller buffers)
+    if kt is None:
+        out_ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+        out_dist = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    else:
+        tot = int(kt.sum().item())
+        out_ids = torch.empty(tot, dtype=torch.int32, device=dev)
+        out_dist = torch.empty(tot, dtype=torch.int32, device=dev)
+
+    def step():
+        return mih.mih_knn(index, queries, karg, out=(out_ids, out_dist))
+
+    for _ in range(a.warmup):
+        r = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device time, max over ranks
+    mih.mih_set_timing(True)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats_acc = {"lookups": 0, "candidates_raw": 0, "candidates_unique": 0, "steps": 0, "phase2_queries": 0,
+                 "waves": 0}
+    main_ms, main_launches, launches = 0.0, 0, 0
+    e0.record()
+    for _ in range(a.steps):
+        r = step()
+        prof = mih.mih_last_profile()
+        main_ms += prof["main_ms"]
+        main_launches += prof["main_launches"]
+        launches += prof["launches"]
+        for key in stats_acc:
+            stats_acc[key] += r["stats"][key]
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    mih.mih_set_timing(False)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / a.steps
+    value = world * nq * a.steps / (ms / 1000.0)
+
+    # ---- roofline of the dominant kernel (fused MIH search), algorithmic bytes
+    sparse = [kd == mih.MIH_TABLE_SPARSE for kd in info["table_kind"]]
+    bytes_per_lookup = 8 + (8 if all(sparse) else 0)       # bucket bounds (+ one {key, rank} slot)
+    bytes_per_cand = 4 + q // 8                            # id + full code
+    alg_bytes = stats_acc["lookups"] * bytes_per_lookup + stats_acc["candidates_raw"] * bytes_per_cand
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = (alg_bytes / max(main_launches, 1)) / ((main_ms / max(main_launches, 1)) / 1000.0) / 1e9 \
+        if main_ms > 0 else None
+    roofline = {"bound": "hbm", "kernel": "search_kernel+search_big_kernel (fused MIH search)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "per_launch_ms": main_ms / max(main_launches, 1), "launches_per_step": main_launches / a.steps,
+                "search_share_of_step": main_ms / ms if ms > 0 else None,
+                "alg_bytes_per_step": alg_bytes / a.steps,
+                "bytes_model": f"{bytes_per_lookup} B/lookup + {bytes_per_cand} B/raw candidate"}
+
+    # ---- end to end through the C-ABI with host buffers (pinned), K steps
+    qh = queries.cpu().pin_memory()
+    ids_h = torch.empty(out_ids.shape, dtype=torch.int32).pin_memory()
+    dist_h = torch.empty(out_dist.shape, dtype=torch.int32).pin_memory()
+    qd = torch.empty_like(queries)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(a.steps):
+        qd.copy_(qh, non_blocking=True)
+        mih.mih_knn(index, qd, karg, out=(out_ids, out_dist))
+        ids_h.copy_(out_ids, non_blocking=True)
+        dist_h.copy_(out_dist, non_blocking=True)
+    f1.record()
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * nq * a.steps / (e2e_ms / 1000.0), "unit": "queries/s",
+           "h2d_bytes_per_step": int(qh.numel() * 8),
+           "d2h_bytes_per_step": int((ids_h.numel() + dist_h.numel()) * 4)}
+
+    # ---- linear scan comparator on the same batch (one timed pass)
+    linscan = None
+    if not a.no_linscan:
+        ls_q = queries[:min(nq, 256)]
+        mih.linscan_knn(codes, q, ls_q, karg if kt is None else kt[:ls_q.shape[0]])   # warm-up
+        torch.cuda.synchronize()
+        mih.mih_set_timing(True)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        ls = mih.linscan_knn(codes, q, queries, karg)
+        g1.record()
+        torch.cuda.synchronize()
+        lprof = mih.mih_last_profile()
+        mih.mih_set_timing(False)
+        ls_ms = g0.elapsed_time(g1)
+        same = bool(torch.equal(ls["ids"], out_ids) and torch.equal(ls["dist"], out_dist))
+        pairs = float(n) * nq
+        linscan = {"value": nq / (ls_ms / 1000.0), "unit": "queries/s", "ms_per_batch": ls_ms,
+                   "mih_speedup": (value / world) / (nq / (ls_ms / 1000.0)),
+                   "identical_to_mih": same, "pairs_per_s": pairs / (ls_ms / 1000.0),
+                   "scan_kernel_ms": lprof["main_ms"]}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1) + sampled parity
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        db_host = codes.cpu().numpy().view(np.uint64)
+        qs_host = queries.cpu().numpy().view(np.uint64)
+        sample = min(a.cpu_sample, nq)
+        qps, cores, dt, res = cpu_oracle_time(db_host, qs_host, kq_np if kq_np is not None else k, sample)
+        cpu = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {sample} queries of the batch over all {n} codes ({dt:.1f} s)"}
+        if kq_np is None:
+            got_ids = out_ids[:sample].cpu().numpy().view(np.uint32)
+            got_d = out_dist[:sample].cpu().numpy()
+            mism = int(np.sum(np.any(got_ids != res[0], axis=1) | np.any(got_d != res[1], axis=1)))
+        else:
+            offs = np.concatenate([[0], np.cumsum(kq_np[:sample].astype(np.int64))])
+            got_ids = out_ids[:offs[-1]].cpu().numpy().view(np.uint32)
+            got_d = out_dist[:offs[-1]].cpu().numpy()
+            mism = int(not (np.array_equal(got_ids, res[1]) and np.array_equal(got_d, res[2])))
+        parity = {"sampled_queries": sample, "mismatched_queries": mism}
+        del db_host
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[a.workload], "n": n, "q": q, "nq_per_gpu": nq,
+                   "k": k if k != "kper" else "log-uniform[1,1000]", "m": m, "codes": kind,
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (codes + tables, no flush)",
+                   "substring_bits": info["substring_length"], "table_kind": info["table_kind"],
+                   "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches, "mih_stats_per_step": {kk: v / a.steps for kk, v in stats_acc.items()},
+        "linscan": linscan, "parity": parity,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    index.free()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -67,7 +67,13 @@ enum {
 
 typedef struct {
     int32_t table_kind;    /* MIH_TABLE_*; DIRECT requires s <= 28 */
-    int32_t reserved[15];  /* must be zero */
+    int32_t scan_factor;   /* A query whose lookups would exceed scan_factor * n
+                              switches to one verification pass over all codes
+                              (results unchanged; lookups are as costly as
+                              candidate tests, Sec. 3).  0 = default (4);
+                              negative = never, which reproduces the lookup
+                              and candidate counts of Algorithms 2 and 3. */
+    int32_t reserved[14];  /* must be zero */
 } mih_params;
 
 /* Aggregate work counters of one mih_knn / mih_rnear call (host struct). */
@@ -203,6 +209,25 @@ MIH_API double mih_cost_model(int q, uint64_t n, int s, int r);
 /* Number of substrings suggested by Sec. 3.1 / Table 4: the integer closest
  * to q / log2(n), clamped so that no substring exceeds 32 bits and m <= q. */
 MIH_API int mih_suggest_m(int q, uint64_t n);
+
+/* ------------------------------------------------------------------------
+ * Per-call profile of the calling host thread (not part of the paper).
+ * With timing enabled, mih_knn, mih_rnear and linscan_knn record CUDA events
+ * on their stream around their main kernels (the fused search kernels, the
+ * linear-scan kernel) and around the whole call.
+ */
+typedef struct {
+    uint64_t launches;       /* kernel launches issued by the last call */
+    uint64_t main_launches;  /* launches of the main kernels */
+    double main_ms;          /* summed device time of the main kernels (timing on) */
+    double call_ms;          /* device time from first to last launch (timing on) */
+} mih_profile;
+
+/* Enable (1) or disable (0) event timing for calls from this host thread. */
+MIH_API void mih_set_timing(int enable);
+
+/* Profile of this thread's last mih_knn / mih_rnear / linscan_knn call. */
+MIH_API mih_status mih_last_profile(mih_profile *out);
 
 /* Static text of a status code. */
 MIH_API const char *mih_status_str(mih_status s);

@@ -133,35 +133,38 @@ static int run_threads(orc_job *proto, int nthreads, void *(*fn)(void *))
  * order the answer is the first min(k, n) entries of the list of all
  * (||h_i - g||_H, i), sorted lexicographically.  Distances are integers in
  * 0..q, so the list is laid out by a counting sort over the distance that is
- * stable in i (ids visited in increasing order).  Slots past n are padded
- * with id 0xFFFFFFFF and distance -1. */
+ * stable in i: one pass counts the codes at each distance, a second pass
+ * visits the ids in increasing order and places each at the next slot of its
+ * distance.  Slots past n are padded with id 0xFFFFFFFF and distance -1. */
 static void *knn_worker(void *arg)
 {
     orc_job *J = (orc_job *)arg;
-    uint16_t *dist = (uint16_t *)malloc((J->n ? J->n : 1) * sizeof(uint16_t));
-    if (!dist) { J->status = -1; return NULL; }
     for (uint64_t qi = (uint64_t)J->tid; qi < J->nq; qi += (uint64_t)J->nthreads) {
         const uint64_t *g = J->queries + qi * J->W;
         uint64_t hist[ORC_MAXQ + 2];
         memset(hist, 0, sizeof(hist));
-        for (uint64_t i = 0; i < J->n; ++i) {
-            dist[i] = (uint16_t)orc_hamming(J->codes + i * J->W, g, J->W);
-            hist[dist[i]]++;
-        }
+        for (uint64_t i = 0; i < J->n; ++i)
+            hist[orc_hamming(J->codes + i * J->W, g, J->W)]++;
         uint64_t k = J->k[qi];
         uint64_t kk = k < J->n ? k : J->n;
         /* start[d] = number of codes closer than d = first sorted slot of d */
         uint64_t start[ORC_MAXQ + 2], acc = 0;
-        for (int d = 0; d <= ORC_MAXQ; ++d) { start[d] = acc; acc += hist[d]; }
+        int dmax = -1;                        /* last distance that reaches a slot < kk */
+        for (int d = 0; d <= ORC_MAXQ; ++d) {
+            start[d] = acc;
+            if (acc < kk) dmax = d;
+            acc += hist[d];
+        }
         uint32_t *oid = J->out_ids + J->out_off[qi];
         int32_t *odist = J->out_dist + J->out_off[qi];
         for (uint64_t i = 0; i < J->n; ++i) {
-            uint64_t p = start[dist[i]]++;
-            if (p < kk) { oid[p] = (uint32_t)i; odist[p] = dist[i]; }
+            int d = orc_hamming(J->codes + i * J->W, g, J->W);
+            if (d > dmax) continue;
+            uint64_t p = start[d]++;
+            if (p < kk) { oid[p] = (uint32_t)i; odist[p] = d; }
         }
         for (uint64_t p = kk; p < k; ++p) { oid[p] = ORC_PAD_ID; odist[p] = -1; }
     }
-    free(dist);
     return NULL;
 }
 

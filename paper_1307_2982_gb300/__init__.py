@@ -28,7 +28,7 @@ PAD_ID = 0xFFFFFFFF
 EXPORTS = (
     "mih_build", "mih_free", "mih_index_get_info", "mih_knn", "mih_rnear", "linscan_knn",
     "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
-    "mih_last_error", "mih_version",
+    "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile",
 )
 
 
@@ -39,7 +39,8 @@ class MihError(RuntimeError):
 
 
 class mih_params(ctypes.Structure):
-    _fields_ = [("table_kind", ctypes.c_int32), ("reserved", ctypes.c_int32 * 15)]
+    _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 14)]
 
 
 class mih_stats(ctypes.Structure):
@@ -48,6 +49,14 @@ class mih_stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class mih_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("main_launches", ctypes.c_uint64),
+                ("main_ms", ctypes.c_double), ("call_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: (float(getattr(self, f)) if "ms" in f else int(getattr(self, f))) for f, _ in self._fields_}
 
 
 class mih_index_info(ctypes.Structure):
@@ -98,6 +107,10 @@ def load():
     lib.mih_last_error.restype = ctypes.c_char_p
     lib.mih_version.argtypes = []
     lib.mih_version.restype = ctypes.c_char_p
+    lib.mih_set_timing.argtypes = [i32]
+    lib.mih_set_timing.restype = None
+    lib.mih_last_profile.argtypes = [P]
+    lib.mih_last_profile.restype = st
     _lib = lib
     return lib
 
@@ -145,6 +158,16 @@ def mih_last_error() -> str:
 
 def mih_version() -> str:
     return load().mih_version().decode()
+
+
+def mih_set_timing(enable: bool):
+    load().mih_set_timing(1 if enable else 0)
+
+
+def mih_last_profile() -> dict:
+    p = mih_profile()
+    _check(load().mih_last_profile(ctypes.byref(p)), "mih_last_profile")
+    return p.as_dict()
 
 
 def mih_substring_layout(q: int, m: int):
@@ -197,10 +220,12 @@ class MihIndex:
             pass
 
 
-def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, stream=None) -> MihIndex:
+def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
+              stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
+    p.scan_factor = scan_factor
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)

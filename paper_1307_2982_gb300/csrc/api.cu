@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <vector>
 
 #include "launch.h"
 
@@ -22,6 +23,82 @@ void set_error(const char* fmt, ...) {
 }
 
 void clear_error() { g_err[0] = '\0'; }
+
+// ---------------------------------------------------------------- profile
+namespace {
+struct Profiler {
+    bool timing = false;
+    int depth = 0;
+    mih_profile last = {0, 0, 0.0, 0.0};
+    mih_profile cur = {0, 0, 0.0, 0.0};
+    std::vector<cudaEvent_t> events;  // pool; pairs [2i, 2i+1] are main-kernel spans
+    size_t used = 0;
+    cudaEvent_t call_start = nullptr, call_stop = nullptr;
+};
+thread_local Profiler g_prof;
+
+cudaEvent_t next_event() {
+    Profiler& p = g_prof;
+    if (p.used == p.events.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p.events.push_back(e);
+    }
+    return p.events[p.used++];
+}
+}  // namespace
+
+void note_launch() { g_prof.cur.launches++; }
+
+void main_kernel_begin(cudaStream_t s) {
+    g_prof.cur.main_launches++;
+    if (!g_prof.timing) return;
+    if (g_prof.used % 2 == 1) return;  // unbalanced: ignore
+    cudaEvent_t e = next_event();
+    if (e) cudaEventRecord(e, s);
+}
+
+void main_kernel_end(cudaStream_t s) {
+    if (!g_prof.timing) return;
+    if (g_prof.used % 2 == 0) return;
+    cudaEvent_t e = next_event();
+    if (e) cudaEventRecord(e, s);
+}
+
+CallScope::CallScope(cudaStream_t s) : s_(s) {
+    Profiler& p = g_prof;
+    if (p.depth++ > 0) return;
+    p.cur = {0, 0, 0.0, 0.0};
+    p.used = 0;
+    if (p.timing) {
+        if (!p.call_start) cudaEventCreate(&p.call_start);
+        if (!p.call_stop) cudaEventCreate(&p.call_stop);
+        cudaEventRecord(p.call_start, s_);
+    }
+}
+
+CallScope::~CallScope() {
+    Profiler& p = g_prof;
+    if (--p.depth > 0) return;
+    if (p.timing && p.call_stop) {
+        cudaEventRecord(p.call_stop, s_);
+        if (cudaEventSynchronize(p.call_stop) == cudaSuccess) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.call_start, p.call_stop) == cudaSuccess) p.cur.call_ms = ms;
+            double main_ms = 0.0;
+            for (size_t i = 0; i + 1 < p.used; i += 2) {
+                float m = 0.f;
+                if (cudaEventElapsedTime(&m, p.events[i], p.events[i + 1]) == cudaSuccess) main_ms += m;
+            }
+            p.cur.main_ms = main_ms;
+        }
+        cudaGetLastError();
+    }
+    p.last = p.cur;
+}
 
 // ------------------------------------------------------------ scratch pool
 namespace {
@@ -173,6 +250,17 @@ const char* mih_status_str(mih_status s) {
 }
 
 const char* mih_last_error(void) { return mih::g_err; }
+
+void mih_set_timing(int enable) { mih::g_prof.timing = enable != 0; }
+
+mih_status mih_last_profile(mih_profile* out) {
+    if (!out) {
+        mih::set_error("mih_last_profile: out is NULL");
+        return MIH_EINVAL;
+    }
+    *out = mih::g_prof.last;
+    return MIH_OK;
+}
 
 const char* mih_version(void) { return "mih-gb300 0.1 (sm_103a)"; }
 

@@ -280,7 +280,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     }
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
-        for (int i = 0; i < 15; ++i)
+        for (int i = 0; i < 14; ++i)
             if (params->reserved[i] != 0) {
                 set_error("mih_build: params.reserved must be zero");
                 return MIH_EINVAL;
@@ -310,6 +310,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->W = q / 64;
     ix->n = n;
     ix->codes = codes;
+    ix->scan_factor = params ? params->scan_factor : 0;
     ix->tables.resize(m);
     ix->distinct_keys.assign(m, 0);
     ix->max_bucket.assign(m, 0);

@@ -19,4 +19,5 @@ struct mih_index {
     std::vector<uint64_t> distinct_keys;        // non-empty buckets per table
     std::vector<uint64_t> max_bucket;           // largest bucket per table
     uint64_t bytes = 0;                         // device bytes owned
+    int scan_factor = 0;                        // lookup budget factor (see mih_params)
 };

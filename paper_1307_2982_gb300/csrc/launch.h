@@ -16,6 +16,20 @@ namespace mih {
 void set_error(const char* fmt, ...);
 void clear_error();
 
+// Per-call profile (mih_last_profile): launch counts and, with timing on,
+// CUDA-event times of the main kernels.  A CallScope brackets one C-ABI call.
+void note_launch();
+void main_kernel_begin(cudaStream_t s);
+void main_kernel_end(cudaStream_t s);
+class CallScope {
+   public:
+    explicit CallScope(cudaStream_t s);
+    ~CallScope();
+
+   private:
+    cudaStream_t s_;
+};
+
 #define MIH_CUDA(call)                                                                    \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
@@ -28,6 +42,7 @@ void clear_error();
 
 #define MIH_LAUNCH_CHECK()                                                                \
     do {                                                                                  \
+        ::mih::note_launch();                                                             \
         cudaError_t e_ = cudaGetLastError();                                              \
         if (e_ != cudaSuccess) {                                                          \
             ::mih::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),  \

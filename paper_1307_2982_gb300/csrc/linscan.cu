@@ -306,6 +306,7 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         return MIH_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallScope scope(s);
     Workspace ws(s);
     uint32_t kmax = 0;
     MIH_TRY(check_k_args(nq, k, k_uniform, out_offsets, out_ids, out_dist, &kmax, ws));
@@ -377,7 +378,9 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         a.cap = cap;
         a.cnt = cnt;
         const dim3 grid(qtiles, static_cast<unsigned>(splits));
+        main_kernel_begin(s);
         MIH_TRY(launch_scan(a, W, G, grid, s));
+        main_kernel_end(s);
 
         finish_first_pass_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, q, n, k, k_uniform, hist, cnt, cap, dk, thr, need,
                                                               n_over);

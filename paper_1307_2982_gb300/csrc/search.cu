@@ -36,6 +36,7 @@ namespace {
 
 constexpr int kSearchThreads = 256;
 constexpr uint32_t kSliceEntries = 1024;   // big-bucket slice
+constexpr uint32_t kScanChunk = 4096;      // codes per chunk of a full verification pass
 constexpr int kQueryShift = 41;            // composite entry: q << 41 | d << 32 | id
 constexpr uint64_t kEntryMask = (1ull << kQueryShift) - 1ull;
 
@@ -70,6 +71,9 @@ struct SearchArgs {
     uint32_t big_cap;
     unsigned int* big_count;
     unsigned int* big_next;
+    const uint8_t* exh;                // per query: verify every code this launch
+    const int32_t* hist_done;          // knn: last step already in the histogram (-1: none)
+    uint64_t n;
 };
 
 // Chunks of step t for a query: ceil(C(s_j, rho) / 256), 0 if rho > s_j.
@@ -89,12 +93,20 @@ __device__ __forceinline__ Code<W> load_query(const uint64_t* __restrict__ queri
 
 // Process one candidate per lane (valid lanes only), warp-synchronous: every
 // lane of the warp calls this together; all valid lanes share query q.
+//
+// Ring mode (j >= 0): the code was reached at step t = m rho + j and is kept
+// only if t is its first step.  Full-pass mode (j < 0): every code is visited
+// once and kept if its first step, min_j' (m d_j' + j'), is after t_done.
+// Either way a kept code enters the histogram and the counters only if its
+// first step is after hist_done (earlier steps were counted before and are
+// revisited only to store their codes under a bound found later).
 template <int W, int MODE>
 __device__ __forceinline__ void handle_candidates(const SearchArgs& a, const int* s_off, const int* s_len,
-                                                  uint32_t q, int j, int rho, const Code<W>& g, bool valid,
-                                                  uint32_t id, uint32_t& unique_acc) {
+                                                  uint32_t q, int j, int rho, int t_done, int hist_done,
+                                                  const Code<W>& g, bool valid, uint32_t id,
+                                                  uint32_t& unique_acc, uint32_t& raw_acc) {
     int d = 0;
-    bool keep = false;
+    bool keep = false, count = false;
     if (valid) {
         const Code<W> c = load_code<W>(a.codes, id);
         Code<W> x;
@@ -102,24 +114,37 @@ __device__ __forceinline__ void handle_candidates(const SearchArgs& a, const int
         for (int w = 0; w < W; ++w) x.w[w] = c.w[w] ^ g.w[w];
 #pragma unroll
         for (int w = 0; w < W; ++w) d += __popcll(x.w[w]);
-        keep = true;
-        for (int jj = 0; jj < a.m; ++jj) {
-            if (jj == j) continue;
-            const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
-            if (jj < j ? (dj <= rho) : (dj < rho)) {
-                keep = false;
-                break;
+        if (j >= 0) {
+            keep = true;
+            for (int jj = 0; jj < a.m; ++jj) {
+                if (jj == j) continue;
+                const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
+                if (jj < j ? (dj <= rho) : (dj < rho)) {
+                    keep = false;
+                    break;
+                }
             }
+            count = a.m * rho + j > hist_done;
+        } else {
+            int first = 0x7FFFFFFF;
+            for (int jj = 0; jj < a.m; ++jj) {
+                const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
+                first = min(first, a.m * dj + jj);
+            }
+            keep = first > t_done;
+            count = first > hist_done;
+            raw_acc += count ? 1u : 0u;
         }
     }
     const uint32_t lane = lane_id();
     const uint32_t lt = (1u << lane) - 1u;
     if constexpr (MODE == kModeKnn) {
-        unique_acc += keep ? 1u : 0u;
+        const bool hit = keep && count;
+        unique_acc += hit ? 1u : 0u;
         // distance histogram, one atomic per distinct distance in the warp
-        const uint32_t hkey = keep ? static_cast<uint32_t>(d) : 0xFFFFu;
+        const uint32_t hkey = hit ? static_cast<uint32_t>(d) : 0xFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, hkey);
-        if (keep && (peers & lt) == 0)
+        if (hit && (peers & lt) == 0)
             atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.q + 1) + d], static_cast<uint32_t>(__popc(peers)));
         const bool store = keep && d <= __ldg(a.bound + q);
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, store);
@@ -149,8 +174,7 @@ __device__ __forceinline__ void handle_candidates(const SearchArgs& a, const int
                 }
             }
         }
-        if constexpr (MODE == kModeCount) unique_acc += keep ? 1u : 0u;
-        if constexpr (MODE == kModeCollect) unique_acc += keep ? 1u : 0u;
+        unique_acc += keep ? 1u : 0u;
     }
 }
 
@@ -158,7 +182,8 @@ __device__ __forceinline__ void handle_candidates(const SearchArgs& a, const int
 template <int W, int MODE>
 __device__ __forceinline__ void scan_buckets(const SearchArgs& a, const int* s_off, const int* s_len,
                                              const uint32_t* __restrict__ ids, uint32_t q, int j, int rho,
-                                             const Code<W>& g, uint32_t b, uint32_t sz, uint32_t& unique_acc) {
+                                             int hist_done, const Code<W>& g, uint32_t b, uint32_t sz,
+                                             uint32_t& unique_acc) {
     const uint32_t incl = warp_inclusive_scan(sz);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t excl = incl - sz;
@@ -175,7 +200,8 @@ __device__ __forceinline__ void scan_buckets(const SearchArgs& a, const int* s_o
         const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
         const bool valid = idx < total;
         const uint32_t id = valid ? __ldg(ids + ob + (idx - oe)) : 0u;
-        handle_candidates<W, MODE>(a, s_off, s_len, q, j, rho, g, valid, id, unique_acc);
+        uint32_t unused = 0;
+        handle_candidates<W, MODE>(a, s_off, s_len, q, j, rho, -1, hist_done, g, valid, id, unique_acc, unused);
     }
 }
 
@@ -204,6 +230,29 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
         const uint32_t q = lo;
         uint64_t lc = c - __ldg(a.chunk_off + q);
         int t = __ldg(a.t_lo + q);
+        const int hd = a.hist_done ? __ldg(a.hist_done + q) : -1;
+        if (a.exh && a.exh[q]) {
+            // Verify codes [lc * kScanChunk, ...) against the query once.
+            const uint64_t base = lc * kScanChunk;
+            const uint64_t end = min(a.n, base + kScanChunk);
+            const Code<W> g = load_query<W>(a.queries, q);
+            uint32_t unique = 0, raw = 0;
+            for (uint64_t p = base; p < end; p += 32) {
+                const bool valid = p + lane < end;
+                handle_candidates<W, MODE>(a, s_off, s_len, q, -1, 0, t - 1, hd, g, valid,
+                                           static_cast<uint32_t>(p + lane), unique, raw);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
+                raw += __shfl_down_sync(0xFFFFFFFFu, raw, o);
+            }
+            if (lane == 0 && a.qstats) {
+                atomicAdd(&a.qstats[4ull * q + 1], static_cast<unsigned long long>(raw));
+                atomicAdd(&a.qstats[4ull * q + 2], static_cast<unsigned long long>(unique));
+            }
+            continue;
+        }
         for (;;) {
             const uint64_t nch = step_chunks(s_len, a.m, t);
             if (lc < nch) break;
@@ -249,10 +298,13 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
             }
             raw += sz;
             if (__any_sync(0xFFFFFFFFu, sz != 0))
-                scan_buckets<W, MODE>(a, s_off, s_len, ids, q, j, rho, g, b, sz, unique);
+                scan_buckets<W, MODE>(a, s_off, s_len, ids, q, j, rho, hd, g, b, sz, unique);
         }
-        // per-query counters (lookups, raw candidates, unique candidates)
-        uint32_t lk = static_cast<uint32_t>(mine);
+        // per-query counters (lookups, raw candidates, unique candidates) of
+        // steps not counted before
+        const bool counting = t > hd;
+        uint32_t lk = counting ? static_cast<uint32_t>(mine) : 0u;
+        if (!counting) raw = 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lk += __shfl_down_sync(0xFFFFFFFFu, lk, o);
@@ -289,11 +341,12 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
         const int j = bs.t % a.m, rho = bs.t / a.m;
         const Code<W> g = load_query<W>(a.queries, bs.q);
         const uint32_t* ids = a.tables[j].ids;
-        uint32_t unique = 0;
+        const int hd = a.hist_done ? __ldg(a.hist_done + bs.q) : -1;
+        uint32_t unique = 0, unused = 0;
         for (uint32_t p = bs.begin; p < bs.end; p += 32) {
             const bool valid = p + lane < bs.end;
             const uint32_t id = valid ? __ldg(ids + p + lane) : 0u;
-            handle_candidates<W, MODE>(a, s_off, s_len, bs.q, j, rho, g, valid, id, unique);
+            handle_candidates<W, MODE>(a, s_off, s_len, bs.q, j, rho, -1, hd, g, valid, id, unique, unused);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
@@ -303,18 +356,28 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
 
 // ------------------------------------------------------------ planning
 // Chunk count of each query's step range [t_lo, t_hi].
-__global__ void plan_chunks_kernel(const TableDesc* __restrict__ tables, int m, uint32_t nq,
+__global__ void plan_chunks_kernel(const TableDesc* __restrict__ tables, int m, uint32_t nq, uint64_t n,
                                    const int32_t* __restrict__ t_lo, const int32_t* __restrict__ t_hi,
-                                   uint64_t* __restrict__ chunks /* [nq + 1] */) {
+                                   const uint8_t* __restrict__ exh, uint64_t* __restrict__ chunks /* [nq + 1] */) {
     __shared__ int s_len[kMaxTables];
     for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
     __syncthreads();
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x) {
         uint64_t c = 0;
-        if (q < nq)
-            for (int t = t_lo[q]; t <= t_hi[q]; ++t) c += step_chunks(s_len, m, t);
+        if (q < nq && t_lo[q] <= t_hi[q]) {
+            if (exh && exh[q]) c = (n + kScanChunk - 1) / kScanChunk;
+            else
+                for (int t = t_lo[q]; t <= t_hi[q]; ++t) c += step_chunks(s_len, m, t);
+        }
         chunks[q] = c;
     }
+}
+
+// Lookups of steps t0..t1 (sum of ring sizes, Eq. 1 per table).
+__device__ __forceinline__ uint64_t steps_lookups(const int* s_len, int m, int t0, int t1) {
+    uint64_t l = 0;
+    for (int t = t0; t <= t1; ++t) l += binom(s_len[t % m], t / m);
+    return l;
 }
 
 __device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform, uint32_t q, uint64_t n) {
@@ -323,10 +386,21 @@ __device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform
 }
 
 // Alg. 3 stopping test after step t_hi[q]; advances or retires each query.
+//
+// A query starts with bound = -1: its steps only fill the histogram.  Once
+// min(k, n) codes are known the bound (an upper bound on the k-th distance)
+// exists; the next launch then revisits steps 0..t to store the codes within
+// the bound (without counting them again) together with step t+1.
 __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32_t* __restrict__ kq,
                                 uint32_t k_uniform, const uint32_t* __restrict__ hist, int32_t* __restrict__ t_lo,
                                 int32_t* __restrict__ t_hi, int32_t* __restrict__ bound, int32_t* __restrict__ dk,
-                                unsigned long long* __restrict__ qstats, unsigned int* __restrict__ active) {
+                                int32_t* __restrict__ hist_done, uint32_t* __restrict__ cnt1, uint32_t cap,
+                                unsigned long long* __restrict__ qstats, unsigned int* __restrict__ active,
+                                const TableDesc* __restrict__ tables, int m, uint8_t* __restrict__ exh,
+                                long long scan_budget) {
+    __shared__ int s_len[kMaxTables];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
+    __syncthreads();
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         const int t = t_hi[q];
         if (t < t_lo[q]) continue;  // retired earlier
@@ -338,14 +412,28 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
             cum += h[d];
             if (first_reach < 0 && cum >= kk) first_reach = d;
         }
-        if (first_reach >= 0 && first_reach <= t) {
-            dk[q] = first_reach;            // all codes within t bits are known
+        const bool full = exh[q] != 0;  // this launch verified every remaining code
+        if (first_reach >= 0 && (first_reach <= t || full)) {
+            dk[q] = first_reach;            // every code within t bits (or all codes) is known
             t_lo[q] = t + 1;
             qstats[4ull * q + 3] = static_cast<unsigned long long>(t);
+            if (bound[q] < 0) cnt1[q] = cap + 1;  // nothing stored yet: second pass collects
         } else {
-            t_lo[q] = t + 1;
+            hist_done[q] = t;
+            if (bound[q] < 0 && first_reach >= 0) {
+                bound[q] = first_reach;
+                t_lo[q] = 0;                // revisit steps 0..t to store under the new bound
+            } else {
+                if (first_reach >= 0) bound[q] = first_reach;
+                t_lo[q] = t + 1;
+            }
             t_hi[q] = t + 1;
-            bound[q] = first_reach >= 0 ? first_reach : qbits;  // upper bound on the k-th distance
+            // Once the next ring alone would push the lookups past the budget,
+            // verifying every remaining code once is cheaper (Sec. 3 cost model:
+            // a lookup costs about one candidate test).
+            if (scan_budget >= 0 &&
+                qstats[4ull * q] + steps_lookups(s_len, m, t + 1, t + 1) > static_cast<unsigned long long>(scan_budget))
+                exh[q] = 1;
             atomicAdd(active, 1u);
         }
     }
@@ -491,7 +579,11 @@ __global__ void phase2_plan_kernel(uint32_t nq, int qbits, const uint32_t* __res
                                    const int32_t* __restrict__ dk, const uint32_t* __restrict__ cnt1, uint32_t cap,
                                    int32_t* __restrict__ t_lo, int32_t* __restrict__ t_hi,
                                    int32_t* __restrict__ bound, uint64_t* __restrict__ need,
-                                   unsigned int* __restrict__ n_over) {
+                                   unsigned int* __restrict__ n_over, const TableDesc* __restrict__ tables, int m,
+                                   uint8_t* __restrict__ exh, long long scan_budget) {
+    __shared__ int s_len[kMaxTables];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
+    __syncthreads();
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q <= nq; q += gridDim.x * blockDim.x) {
         if (q == nq) { need[q] = 0; continue; }
         const bool over = cnt1[q] > cap;
@@ -505,16 +597,19 @@ __global__ void phase2_plan_kernel(uint32_t nq, int qbits, const uint32_t* __res
         t_lo[q] = 0;
         t_hi[q] = over ? dk[q] : -1;
         bound[q] = dk[q];
+        exh[q] = (over && scan_budget >= 0 &&
+                  steps_lookups(s_len, m, 0, dk[q]) > static_cast<unsigned long long>(scan_budget)) ? 1 : 0;
     }
 }
 
 __global__ void init_knn_kernel(uint32_t nq, uint64_t n, int32_t* t_lo, int32_t* t_hi, int32_t* bound,
-                                int32_t* dk, int qbits) {
+                                int32_t* dk, int32_t* hist_done) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         t_lo[q] = 0;
         t_hi[q] = n > 0 ? 0 : -1;
-        bound[q] = qbits;
+        bound[q] = -1;
         dk[q] = 0;
+        hist_done[q] = -1;
     }
 }
 
@@ -602,7 +697,8 @@ template <int MODE>
 mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
                     const DeviceInfo& dev, Workspace& ws) {
     cudaStream_t s = ws.stream();
-    plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, t_lo, t_hi, p.chunk_off);
+    plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
+                                                      p.chunk_off);
     MIH_LAUNCH_CHECK();
     MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
     MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
@@ -614,7 +710,25 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
     a.big_cap = p.big_cap;
     a.big_count = reinterpret_cast<unsigned int*>(p.counters + 1);
     a.big_next = a.big_count + 1;
-    return launch_search<MODE>(a, ix->W, dev, s);
+    main_kernel_begin(s);
+    const mih_status st = launch_search<MODE>(a, ix->W, dev, s);
+    main_kernel_end(s);
+    return st;
+}
+
+// Lookups after which a query switches to one verification pass over all
+// codes: scan_factor * n (default 4 n); -1 = never.
+long long scan_budget(const mih_index* ix) {
+    if (ix->scan_factor < 0) return -1;
+    const long long f = ix->scan_factor == 0 ? 4 : ix->scan_factor;
+    return f * static_cast<long long>(ix->n);
+}
+
+unsigned long long host_binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    unsigned long long c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return c;
 }
 
 mih_status check_flag(const int* err, const char* what, cudaStream_t s) {
@@ -752,8 +866,9 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
                    mih_stats* stats, void* stream) {
     clear_error();
     if (stats) memset(stats, 0, sizeof(*stats));
-    MIH_TRY(validate_common(ix, queries, nq));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallScope scope(s);
+    MIH_TRY(validate_common(ix, queries, nq));
     Workspace ws(s);
     uint32_t kmax = 0;
     MIH_TRY(check_k_args(nq, k, k_uniform, out_offsets, out_ids, out_dist, &kmax, ws));
@@ -778,10 +893,16 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_TRY(ws.alloc(&buf1, static_cast<size_t>(nq) * cap));
     MIH_TRY(ws.alloc(&qstats, 4ull * nq));
     MIH_TRY(ws.alloc(&active, 1));
+    uint8_t* exh;
+    MIH_TRY(ws.alloc(&exh, nq));
+    MIH_CUDA(cudaMemsetAsync(exh, 0, nq, s));
+    const long long budget = scan_budget(ix);
     MIH_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nq * (qb + 1), s));
     MIH_CUDA(cudaMemsetAsync(cnt1, 0, sizeof(uint32_t) * nq, s));
     MIH_CUDA(cudaMemsetAsync(qstats, 0, sizeof(unsigned long long) * 4 * nq, s));
-    init_knn_kernel<<<grid1(nq), 256, 0, s>>>(nq, ix->n, t_lo, t_hi, bound, dk, qb);
+    int32_t* hist_done;
+    MIH_TRY(ws.alloc(&hist_done, nq));
+    init_knn_kernel<<<grid1(nq), 256, 0, s>>>(nq, ix->n, t_lo, t_hi, bound, dk, hist_done);
     MIH_LAUNCH_CHECK();
     Plan plan;
     MIH_TRY(plan_alloc(plan, nq, ws));
@@ -800,6 +921,9 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     a.cap = cap;
     a.cnt = cnt1;
     a.qstats = qstats;
+    a.exh = exh;
+    a.hist_done = hist_done;
+    a.n = ix->n;
 
     uint64_t waves = 0;
     if (ix->n > 0) {
@@ -808,7 +932,8 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
             ++waves;
             MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), s));
             knn_stop_kernel<<<grid1(nq), 256, 0, s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
-                                                     qstats, active);
+                                                     hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
+                                                     exh, budget);
             MIH_LAUNCH_CHECK();
             unsigned int hact = 0;
             MIH_CUDA(cudaMemcpyAsync(&hact, active, sizeof(hact), cudaMemcpyDeviceToHost, s));
@@ -827,7 +952,8 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_TRY(ws.alloc(&need, static_cast<size_t>(nq) + 1));
     MIH_TRY(ws.alloc(&n_over, 1));
     MIH_CUDA(cudaMemsetAsync(n_over, 0, sizeof(unsigned int), s));
-    phase2_plan_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, qb, hist, dk, cnt1, cap, t_lo, t_hi, bound, need, n_over);
+    phase2_plan_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, qb, hist, dk, cnt1, cap, t_lo, t_hi, bound, need, n_over,
+                                                    ix->dev_tables, ix->m, exh, budget);
     MIH_LAUNCH_CHECK();
     unsigned int hover = 0;
     MIH_CUDA(cudaMemcpyAsync(&hover, n_over, sizeof(hover), cudaMemcpyDeviceToHost, s));
@@ -850,6 +976,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         b.cnt = cursor;
         b.out_base = need;
         b.qstats = nullptr;
+        b.hist_done = nullptr;
         b.err = err;
         MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
         ++waves;
@@ -900,6 +1027,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
     clear_error();
     if (stats) memset(stats, 0, sizeof(*stats));
     if (total_out) *total_out = 0;
+    CallScope scope(static_cast<cudaStream_t>(stream));
     MIH_TRY(validate_common(ix, queries, nq));
     if (r < 0) {
         set_error("mih_rnear: r must be >= 0");
@@ -941,6 +1069,21 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
     a.bound = bound;
     a.cnt = cnt;
     a.qstats = qstats;
+    a.n = ix->n;
+    uint8_t* exh;
+    MIH_TRY(ws.alloc(&exh, nqa));
+    {
+        // Alg. 2 is steps 0..r; past the lookup budget one verification pass
+        // over all codes replaces them.
+        const long long budget = scan_budget(ix);
+        unsigned long long lk = 0;
+        for (int t = 0; t <= reff; ++t) {
+            const int s_j = ix->tables[t % ix->m].len, rho = t / ix->m;
+            lk += rho <= s_j ? host_binom(s_j, rho) : 0ull;
+        }
+        MIH_CUDA(cudaMemsetAsync(exh, (budget >= 0 && lk > static_cast<unsigned long long>(budget)) ? 1 : 0, nqa, s));
+    }
+    a.exh = exh;
     if (nq > 0 && ix->n > 0) {
         init_range_kernel<<<grid1(nq), 256, 0, s>>>(nq, 0, reff, reff, t_lo, t_hi, bound);
         MIH_LAUNCH_CHECK();
