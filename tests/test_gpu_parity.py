@@ -95,7 +95,7 @@ def test_table_kinds_agree(gpu_lib, orc, table_kind):
 
 
 @pytest.mark.parametrize("kind,q,m,n", [("uniform", 64, 4, 20_000), ("lsh", 128, 6, 20_000),
-                                        ("ties", 64, 3, 5_000), ("lsh", 256, 9, 8_000)])
+                                        ("ties", 64, 3, 5_000), ("lsh", 256, 12, 8_000)])
 def test_mih_work_counters_match_alg3(gpu_lib, orc, kind, q, m, n):
     """Per-query lookups, raw/unique candidates and last step equal Alg. 3 on the CPU."""
     mih = gpu_lib
