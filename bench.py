@@ -71,6 +71,14 @@ def parse():
     return a
 
 
+def workload_name(a):
+    kind, n, q, nq, k, m = workload(a)
+    if (n, nq, k) == WORKLOADS[a.workload][1:2] + WORKLOADS[a.workload][3:5]:
+        return WORKLOAD_NAMES[a.workload]
+    ks = "k log-uniform [1,1000]" if k == "kper" else f"k={k}"
+    return f"{n:.0e} x {q}-bit {'LSH-style' if kind == 'lsh' else 'uniform'} codes, {nq} queries, {ks}"
+
+
 def workload(a):
     kind, n, q, nq, k, m = WORKLOADS[a.workload]
     n = a.n or n
@@ -207,7 +215,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * dt / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAMES[a.workload], "n": n, "q": q, "nq": nq, "k": k if k != "kper" else
+        "config": {"workload": workload_name(a), "n": n, "q": q, "nq": nq, "k": k if k != "kper" else
                    "log-uniform[1,1000]", "codes": kind},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
                          "sample": f"{sample} queries per step over all {n} codes"},
@@ -243,6 +251,7 @@ def run_ours(a):
     kt = torch.from_numpy(kq_np.astype(np.int32)).to(dev) if kq_np is not None else None
     karg = kt if kt is not None else k
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()      # hand the generator's cached blocks back before the build
     gen_s = time.perf_counter() - t0
 
     # index build (Algorithm 1), timed on the device
@@ -401,7 +410,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAMES[a.workload], "n": n, "q": q, "nq_per_gpu": nq,
+        "config": {"workload": workload_name(a), "n": n, "q": q, "nq_per_gpu": nq,
                    "k": k if k != "kper" else "log-uniform[1,1000]", "m": m, "codes": kind,
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (codes + tables, no flush)",
                    "substring_bits": info["substring_length"], "table_kind": info["table_kind"],

@@ -73,7 +73,12 @@ typedef struct {
                               candidate tests, Sec. 3).  0 = default (4);
                               negative = never, which reproduces the lookup
                               and candidate counts of Algorithms 2 and 3. */
-    int32_t reserved[14];  /* must be zero */
+    int32_t inline_codes;  /* Keep a copy of the codes in each table's bucket order
+                              (m * n * q/8 extra bytes) so that a bucket's
+                              candidates are one contiguous read.  0 = auto (when
+                              ids and inline codes fit in 60% of the free
+                              device memory), 1 = always, negative = never. */
+    int32_t reserved[13];  /* must be zero */
 } mih_params;
 
 /* Aggregate work counters of one mih_knn / mih_rnear call (host struct). */
@@ -95,6 +100,7 @@ typedef struct {
     uint64_t distinct_keys[256];    /* non-empty buckets of table j */
     uint64_t max_bucket[256];       /* largest bucket of table j */
     uint64_t index_bytes;           /* device bytes owned by the index */
+    int32_t inline_codes;           /* 1 if the tables hold codes in bucket order */
 } mih_index_info;
 
 /* ------------------------------------------------------------------------

@@ -40,7 +40,7 @@ class MihError(RuntimeError):
 
 class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 14)]
+                ("inline_codes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 13)]
 
 
 class mih_stats(ctypes.Structure):
@@ -64,7 +64,7 @@ class mih_index_info(ctypes.Structure):
                 ("substring_offset", ctypes.c_int32 * 256), ("substring_length", ctypes.c_int32 * 256),
                 ("table_kind", ctypes.c_int32 * 256), ("n", ctypes.c_uint64),
                 ("distinct_keys", ctypes.c_uint64 * 256), ("max_bucket", ctypes.c_uint64 * 256),
-                ("index_bytes", ctypes.c_uint64)]
+                ("index_bytes", ctypes.c_uint64), ("inline_codes", ctypes.c_int32)]
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -206,6 +206,7 @@ class MihIndex:
             "table_kind": list(inf.table_kind)[:m],
             "distinct_keys": [int(x) for x in list(inf.distinct_keys)[:m]],
             "max_bucket": [int(x) for x in list(inf.max_bucket)[:m]],
+            "inline_codes": int(inf.inline_codes),
         }
 
     def free(self):
@@ -221,11 +222,12 @@ class MihIndex:
 
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
-              stream=None) -> MihIndex:
+              inline_codes: int = 0, stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
     p.scan_factor = scan_factor
+    p.inline_codes = inline_codes
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)

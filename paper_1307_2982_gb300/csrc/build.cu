@@ -40,6 +40,18 @@ __global__ void extract_keys_kernel(const uint64_t* __restrict__ codes, uint64_t
     }
 }
 
+// codes_out[p] = codes[ids[p]]: the table's codes in bucket order.
+template <int W>
+__global__ void gather_codes_kernel(const uint64_t* __restrict__ codes, const uint32_t* __restrict__ ids, uint64_t n,
+                                    uint64_t* __restrict__ out) {
+    for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const Code<W> c = load_code<W>(codes, __ldg(ids + p));
+#pragma unroll
+        for (int w = 0; w < W; ++w) out[p * W + w] = c.w[w];
+    }
+}
+
 __global__ void count_keys_kernel(const uint32_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ counts) {
     for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
@@ -175,6 +187,16 @@ mih_status build_table(mih_index* ix, int j, int kind, const DeviceInfo& dev, cu
     if (sids != ids && n > 0) MIH_CUDA(cudaMemcpyAsync(ids, sids, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
     t.ids = ids;
     t.kind = kind;
+    t.codes = nullptr;
+    if (ix->inline_codes && n > 0) {
+        uint64_t* inl;
+        MIH_TRY(index_alloc(ix, reinterpret_cast<void**>(&inl), n * ix->W * sizeof(uint64_t)));
+        if (ix->W == 1) gather_codes_kernel<1><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, inl);
+        else if (ix->W == 2) gather_codes_kernel<2><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, inl);
+        else gather_codes_kernel<4><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, inl);
+        MIH_LAUNCH_CHECK();
+        t.codes = inl;
+    }
 
     unsigned long long* stats;  // [distinct, max bucket]
     MIH_TRY(ws.alloc(&stats, 2));
@@ -280,7 +302,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     }
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
-        for (int i = 0; i < 14; ++i)
+        for (int i = 0; i < 13; ++i)
             if (params->reserved[i] != 0) {
                 set_error("mih_build: params.reserved must be zero");
                 return MIH_EINVAL;
@@ -311,6 +333,24 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->n = n;
     ix->codes = codes;
     ix->scan_factor = params ? params->scan_factor : 0;
+    {
+        // Inline codes: m * n * q/8 bytes on top of ids (4 m n) and tables;
+        // automatic when the whole index fits in half the free memory.
+        const int req = params ? params->inline_codes : 0;
+        if (req > 0) {
+            ix->inline_codes = true;
+        } else if (req == 0 && n > 0) {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+                cudaGetLastError();
+                free_b = 0;
+            }
+            // ids (4 B) + inline codes (q/8 B) per entry and table, plus the
+            // build's transient key/id buffers (12 B per code)
+            const double est = static_cast<double>(m) * n * (q / 8 + 4) + 12.0 * n;
+            ix->inline_codes = est < 0.6 * static_cast<double>(free_b);
+        }
+    }
     ix->tables.resize(m);
     ix->distinct_keys.assign(m, 0);
     ix->max_bucket.assign(m, 0);
@@ -379,6 +419,7 @@ mih_status mih_index_get_info(const mih_index* ix, mih_index_info* info) {
     info->W = ix->W;
     info->n = ix->n;
     info->index_bytes = ix->bytes;
+    info->inline_codes = ix->inline_codes ? 1 : 0;
     for (int j = 0; j < ix->m; ++j) {
         info->substring_offset[j] = ix->tables[j].off;
         info->substring_length[j] = ix->tables[j].len;

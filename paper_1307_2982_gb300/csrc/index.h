@@ -20,4 +20,5 @@ struct mih_index {
     std::vector<uint64_t> max_bucket;           // largest bucket per table
     uint64_t bytes = 0;                         // device bytes owned
     int scan_factor = 0;                        // lookup budget factor (see mih_params)
+    bool inline_codes = false;                  // tables hold codes in bucket order
 };

@@ -31,6 +31,7 @@ struct TableDesc {
     uint64_t bucket_mask;      // sparse: nbuckets - 1 (power of two)
     uint32_t max_probe;        // sparse: longest probe sequence at build
     uint32_t pad2_;
+    const uint64_t* codes;     // optional: codes in the order of `ids` (W words each)
 };
 
 // ---------------------------------------------------------------- binomials

@@ -91,130 +91,205 @@ __device__ __forceinline__ Code<W> load_query(const uint64_t* __restrict__ queri
     return g;
 }
 
-// Process one candidate per lane (valid lanes only), warp-synchronous: every
-// lane of the warp calls this together; all valid lanes share query q.
+// Distance of one candidate and its duplicate test.
 //
 // Ring mode (j >= 0): the code was reached at step t = m rho + j and is kept
-// only if t is its first step.  Full-pass mode (j < 0): every code is visited
-// once and kept if its first step, min_j' (m d_j' + j'), is after t_done.
-// Either way a kept code enters the histogram and the counters only if its
-// first step is after hist_done (earlier steps were counted before and are
-// revisited only to store their codes under a bound found later).
-template <int W, int MODE>
-__device__ __forceinline__ void handle_candidates(const SearchArgs& a, const int* s_off, const int* s_len,
-                                                  uint32_t q, int j, int rho, int t_done, int hist_done,
-                                                  const Code<W>& g, bool valid, uint32_t id,
-                                                  uint32_t& unique_acc, uint32_t& raw_acc) {
-    int d = 0;
-    bool keep = false, count = false;
-    if (valid) {
-        const Code<W> c = load_code<W>(a.codes, id);
-        Code<W> x;
+// only if t is its first step (no table j' < j within rho bits, none j' > j
+// within rho - 1).  Full-pass mode (j < 0): every code is visited once and
+// kept if its first step, min_j' (m d_j' + j'), is after t_done.  Either way
+// a kept code enters the histogram and the counters only if its first step is
+// after hist_done (steps up to hist_done were counted before and are revisited
+// only to store their codes under a bound found later).
+template <int W>
+__device__ __forceinline__ void eval_candidate(int m, const int* s_off, const int* s_len, int j, int rho,
+                                               int t_done, int hist_done, const Code<W>& g, const Code<W>& c,
+                                               int& d, bool& keep, bool& count) {
+    Code<W> x;
 #pragma unroll
-        for (int w = 0; w < W; ++w) x.w[w] = c.w[w] ^ g.w[w];
+    for (int w = 0; w < W; ++w) x.w[w] = c.w[w] ^ g.w[w];
+    d = 0;
 #pragma unroll
-        for (int w = 0; w < W; ++w) d += __popcll(x.w[w]);
-        if (j >= 0) {
-            keep = true;
-            for (int jj = 0; jj < a.m; ++jj) {
-                if (jj == j) continue;
-                const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
-                if (jj < j ? (dj <= rho) : (dj < rho)) {
-                    keep = false;
-                    break;
-                }
-            }
-            count = a.m * rho + j > hist_done;
-        } else {
-            int first = 0x7FFFFFFF;
-            for (int jj = 0; jj < a.m; ++jj) {
-                const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
-                first = min(first, a.m * dj + jj);
-            }
-            keep = first > t_done;
-            count = first > hist_done;
-            raw_acc += count ? 1u : 0u;
-        }
-    }
-    const uint32_t lane = lane_id();
-    const uint32_t lt = (1u << lane) - 1u;
-    if constexpr (MODE == kModeKnn) {
-        const bool hit = keep && count;
-        unique_acc += hit ? 1u : 0u;
-        // distance histogram, one atomic per distinct distance in the warp
-        const uint32_t hkey = hit ? static_cast<uint32_t>(d) : 0xFFFFu;
-        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, hkey);
-        if (hit && (peers & lt) == 0)
-            atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.q + 1) + d], static_cast<uint32_t>(__popc(peers)));
-        const bool store = keep && d <= __ldg(a.bound + q);
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, store);
-        if (bal) {
-            uint32_t base = 0;
-            const int leader = __ffs(bal) - 1;
-            if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
-            base = __shfl_sync(0xFFFFFFFFu, base, leader);
-            if (store) {
-                const uint32_t p = base + __popc(bal & lt);
-                if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, id);
+    for (int w = 0; w < W; ++w) d += __popcll(x.w[w]);
+    if (j >= 0) {
+        keep = true;
+        for (int jj = 0; jj < m; ++jj) {
+            if (jj == j) continue;
+            const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
+            if (jj < j ? (dj <= rho) : (dj < rho)) {
+                keep = false;
+                break;
             }
         }
+        count = m * rho + j > hist_done;
     } else {
-        const bool take = keep && d <= __ldg(a.bound + q);
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
-        if (bal) {
-            const int leader = __ffs(bal) - 1;
-            uint32_t base = 0;
-            if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
-            if constexpr (MODE == kModeCollect) {
-                base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                if (take) {
-                    const uint64_t p = __ldg(a.out_base + q) + base + __popc(bal & lt);
-                    if (p < __ldg(a.out_base + q + 1)) a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(d, id);
-                    else atomicExch(a.err, 1);
-                }
-            }
+        int first = 0x7FFFFFFF;
+        for (int jj = 0; jj < m; ++jj) {
+            const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
+            first = min(first, m * dj + jj);
         }
-        unique_acc += keep ? 1u : 0u;
+        keep = first > t_done;
+        count = first > hist_done;
     }
 }
 
-// Warp-cooperative pass over the union of up to 32 buckets [b, b + sz).
-template <int W, int MODE>
+// Where a batch of candidates lives.  Candidate positions index either a
+// table's entries (its ids, and its codes in bucket order when the index keeps
+// them inline) or, for a full pass, the code array itself (id = position).
+struct CandSource {
+    const uint64_t* codes;  // codes by position (inline) or by id (base array)
+    const uint32_t* ids;    // ids by position, or null when id = position
+    bool by_id;             // codes are indexed by id: load the id first
+};
+
+// B candidates per lane, warp-synchronous (all 32 lanes call together; every
+// valid candidate belongs to query q).  All B loads of a kind are issued
+// before any is used, so each lane keeps B gathers in flight.  With inline
+// codes the id is read only for candidates that are stored.  Kept distances
+// go to the warp's shared-memory histogram `whist` (flushed by flush_hist).
+template <int W, int MODE, int B>
+__device__ __forceinline__ void handle_batch(const SearchArgs& a, const int* s_off, const int* s_len,
+                                             uint32_t* whist, uint32_t q, int j, int rho, int t_done, int hist_done,
+                                             int bnd, const Code<W>& g, const CandSource& src,
+                                             const uint32_t (&pos)[B], const bool (&valid)[B],
+                                             uint32_t& unique_acc, uint32_t& raw_acc) {
+    Code<W> c[B];
+    uint32_t id[B];
+    if (src.by_id) {
+#pragma unroll
+        for (int b = 0; b < B; ++b) id[b] = valid[b] ? __ldg(src.ids + pos[b]) : 0u;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (valid[b]) c[b] = load_code<W>(src.codes, id[b]);
+            else
+#pragma unroll
+                for (int w = 0; w < W; ++w) c[b].w[w] = 0ull;
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            id[b] = pos[b];
+            if (valid[b]) c[b] = load_code<W>(src.codes, pos[b]);
+            else
+#pragma unroll
+                for (int w = 0; w < W; ++w) c[b].w[w] = 0ull;
+        }
+    }
+    const bool lazy_id = !src.by_id && src.ids != nullptr;
+    const uint32_t lane = lane_id();
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        int d = 0;
+        bool keep = false, count = false;
+        if (valid[b]) eval_candidate<W>(a.m, s_off, s_len, j, rho, t_done, hist_done, g, c[b], d, keep, count);
+        if (j < 0) raw_acc += (valid[b] && count) ? 1u : 0u;
+        if constexpr (MODE == kModeKnn) {
+            if (keep && count) {
+                atomicAdd(&whist[d], 1u);
+                ++unique_acc;
+            }
+            const bool store = keep && d <= bnd;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, store);
+            if (bal) {
+                uint32_t base = 0;
+                const int leader = __ffs(bal) - 1;
+                if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
+                base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                if (store) {
+                    const uint32_t p = base + __popc(bal & lt);
+                    const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
+                    if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, cid);
+                }
+            }
+        } else {
+            const bool take = keep && d <= bnd;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
+            if (bal) {
+                const int leader = __ffs(bal) - 1;
+                uint32_t base = 0;
+                if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
+                if constexpr (MODE == kModeCollect) {
+                    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+                    if (take) {
+                        const uint64_t p = __ldg(a.out_base + q) + base + __popc(bal & lt);
+                        const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
+                        if (p < __ldg(a.out_base + q + 1))
+                            a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(d, cid);
+                        else
+                            atomicExch(a.err, 1);
+                    }
+                }
+            }
+            unique_acc += keep ? 1u : 0u;
+        }
+    }
+}
+
+// Add the warp's histogram to query q's global histogram and clear it.
+__device__ __forceinline__ void flush_hist(uint32_t* whist, uint32_t* ghist, int qbits) {
+    __syncwarp();
+    for (int d = lane_id(); d <= qbits; d += 32) {
+        const uint32_t v = whist[d];
+        if (v) {
+            atomicAdd(ghist + d, v);
+            whist[d] = 0;
+        }
+    }
+    __syncwarp();
+}
+
+// Warp-cooperative pass over the union of up to 32 buckets [b, b + sz),
+// 32 * B candidates per round.
+template <int W, int MODE, int B>
 __device__ __forceinline__ void scan_buckets(const SearchArgs& a, const int* s_off, const int* s_len,
-                                             const uint32_t* __restrict__ ids, uint32_t q, int j, int rho,
-                                             int hist_done, const Code<W>& g, uint32_t b, uint32_t sz,
-                                             uint32_t& unique_acc) {
+                                             uint32_t* whist, const CandSource& src, uint32_t q, int j,
+                                             int rho, int hist_done, int bnd, const Code<W>& g, uint32_t b,
+                                             uint32_t sz, uint32_t& unique_acc) {
     const uint32_t incl = warp_inclusive_scan(sz);
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     const uint32_t excl = incl - sz;
     const uint32_t lane = lane_id();
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t idx = base + lane;
-        int owner = 0;
+    for (uint32_t base = 0; base < total; base += 32 * B) {
+        uint32_t pos[B];
+        bool valid[B];
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
-            if (e <= idx) owner += step;
+        for (int k = 0; k < B; ++k) {
+            const uint32_t idx = base + k * 32 + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
+                if (e <= idx) owner += step;
+            }
+            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, b, owner);
+            const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
+            valid[k] = idx < total;
+            pos[k] = valid[k] ? ob + (idx - oe) : 0u;
         }
-        const uint32_t ob = __shfl_sync(0xFFFFFFFFu, b, owner);
-        const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
-        const bool valid = idx < total;
-        const uint32_t id = valid ? __ldg(ids + ob + (idx - oe)) : 0u;
         uint32_t unused = 0;
-        handle_candidates<W, MODE>(a, s_off, s_len, q, j, rho, -1, hist_done, g, valid, id, unique_acc, unused);
+        handle_batch<W, MODE, B>(a, s_off, s_len, whist, q, j, rho, -1, hist_done, bnd, g, src, pos, valid,
+                                 unique_acc, unused);
     }
 }
+
+constexpr int kBatch = 4;      // candidates in flight per lane, bucket unions
+constexpr int kBigBatch = 8;   // candidates in flight per lane, big-bucket slices
+constexpr int kWarps = kSearchThreads / 32;
+constexpr int kHistBins = 257; // distances 0..256
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
     __shared__ int s_off[kMaxTables];
     __shared__ int s_len[kMaxTables];
+    __shared__ uint32_t s_hist[kWarps][kHistBins];
     for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
         s_off[j] = a.tables[j].off;
         s_len[j] = a.tables[j].len;
     }
+    for (int i = threadIdx.x; i < kWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t lane = lane_id();
+    uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned long long total_chunks = a.chunk_off[a.nq];
     for (;;) {
         unsigned long long c = 0;
@@ -231,17 +306,28 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
         uint64_t lc = c - __ldg(a.chunk_off + q);
         int t = __ldg(a.t_lo + q);
         const int hd = a.hist_done ? __ldg(a.hist_done + q) : -1;
+        const int bnd = __ldg(a.bound + q);
+        uint32_t* ghist = (MODE == kModeKnn) ? a.hist + static_cast<uint64_t>(q) * (a.q + 1) : nullptr;
         if (a.exh && a.exh[q]) {
             // Verify codes [lc * kScanChunk, ...) against the query once.
             const uint64_t base = lc * kScanChunk;
             const uint64_t end = min(a.n, base + kScanChunk);
             const Code<W> g = load_query<W>(a.queries, q);
             uint32_t unique = 0, raw = 0;
-            for (uint64_t p = base; p < end; p += 32) {
-                const bool valid = p + lane < end;
-                handle_candidates<W, MODE>(a, s_off, s_len, q, -1, 0, t - 1, hd, g, valid,
-                                           static_cast<uint32_t>(p + lane), unique, raw);
+            const CandSource src{a.codes, nullptr, false};
+            for (uint64_t p = base; p < end; p += 32 * kBigBatch) {
+                uint32_t pos[kBigBatch];
+                bool valid[kBigBatch];
+#pragma unroll
+                for (int k = 0; k < kBigBatch; ++k) {
+                    const uint64_t i = p + k * 32 + lane;
+                    valid[k] = i < end;
+                    pos[k] = static_cast<uint32_t>(i);
+                }
+                handle_batch<W, MODE, kBigBatch>(a, s_off, s_len, whist, q, -1, 0, t - 1, hd, bnd, g, src, pos,
+                                                 valid, unique, raw);
             }
+            if (MODE == kModeKnn) flush_hist(whist, ghist, a.q);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
@@ -267,7 +353,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
         const Code<W> g = load_query<W>(a.queries, q);
         const uint32_t gkey = substring_bits<W>(g, s_off[j], s);
         const TableDesc& tab = a.tables[j];
-        const uint32_t* ids = tab.ids;
+        const CandSource src = tab.codes ? CandSource{tab.codes, tab.ids, false} : CandSource{a.codes, tab.ids, true};
         uint64_t x = mine > 0 ? unrank_subset(first, s, rho) : 0ull;
         uint32_t raw = 0, unique = 0;
         for (int r = 0; r < kKeysPerLane; ++r) {
@@ -298,8 +384,9 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
             }
             raw += sz;
             if (__any_sync(0xFFFFFFFFu, sz != 0))
-                scan_buckets<W, MODE>(a, s_off, s_len, ids, q, j, rho, hd, g, b, sz, unique);
+                scan_buckets<W, MODE, kBatch>(a, s_off, s_len, whist, src, q, j, rho, hd, bnd, g, b, sz, unique);
         }
+        if (MODE == kModeKnn) flush_hist(whist, ghist, a.q);
         // per-query counters (lookups, raw candidates, unique candidates) of
         // steps not counted before
         const bool counting = t > hd;
@@ -319,17 +406,20 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
     }
 }
 
-// Slices of large buckets, one warp per slice.
+// Slices of large buckets, one warp per slice, 32 * kBigBatch entries per round.
 template <int W, int MODE>
 __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a) {
     __shared__ int s_off[kMaxTables];
     __shared__ int s_len[kMaxTables];
+    __shared__ uint32_t s_hist[kWarps][kHistBins];
     for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
         s_off[j] = a.tables[j].off;
         s_len[j] = a.tables[j].len;
     }
+    for (int i = threadIdx.x; i < kWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     __syncthreads();
     const uint32_t lane = lane_id();
+    uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned int count = min(*a.big_count, a.big_cap);
     for (;;) {
         unsigned int i = 0;
@@ -340,14 +430,24 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
         if (bs.q == kPadId) continue;
         const int j = bs.t % a.m, rho = bs.t / a.m;
         const Code<W> g = load_query<W>(a.queries, bs.q);
-        const uint32_t* ids = a.tables[j].ids;
+        const TableDesc& tab = a.tables[j];
+        const CandSource src = tab.codes ? CandSource{tab.codes, tab.ids, false} : CandSource{a.codes, tab.ids, true};
         const int hd = a.hist_done ? __ldg(a.hist_done + bs.q) : -1;
+        const int bnd = __ldg(a.bound + bs.q);
         uint32_t unique = 0, unused = 0;
-        for (uint32_t p = bs.begin; p < bs.end; p += 32) {
-            const bool valid = p + lane < bs.end;
-            const uint32_t id = valid ? __ldg(ids + p + lane) : 0u;
-            handle_candidates<W, MODE>(a, s_off, s_len, bs.q, j, rho, -1, hd, g, valid, id, unique, unused);
+        for (uint32_t p = bs.begin; p < bs.end; p += 32 * kBigBatch) {
+            uint32_t pos[kBigBatch];
+            bool valid[kBigBatch];
+#pragma unroll
+            for (int k = 0; k < kBigBatch; ++k) {
+                const uint32_t e = p + k * 32 + lane;
+                valid[k] = e < bs.end;
+                pos[k] = e;
+            }
+            handle_batch<W, MODE, kBigBatch>(a, s_off, s_len, whist, bs.q, j, rho, -1, hd, bnd, g, src, pos, valid,
+                                             unique, unused);
         }
+        if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(bs.q) * (a.q + 1), a.q);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
         if (lane == 0 && a.qstats) atomicAdd(&a.qstats[4ull * bs.q + 2], static_cast<unsigned long long>(unique));
@@ -849,8 +949,8 @@ mih_status launch_select(const SelectInputs& in, Workspace& ws) {
 }
 
 uint32_t knn_buffer_cap(uint32_t kmax) {
-    uint64_t c = 8ull * kmax;
-    if (c < 1024) c = 1024;
+    uint64_t c = 16ull * kmax;
+    if (c < 4096) c = 4096;
     if (c > 65536) c = 65536;
     return static_cast<uint32_t>(c);
 }

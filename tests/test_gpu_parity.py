@@ -78,15 +78,16 @@ def test_linscan_and_mih_knn_match_oracle(gpu_lib, orc, kind, q, n, nq, ms):
         ix.free()
 
 
-@pytest.mark.parametrize("table_kind", [1, 2])
-def test_table_kinds_agree(gpu_lib, orc, table_kind):
-    """Direct and sparse tables (Sec. 6) give the same answers."""
+@pytest.mark.parametrize("table_kind,inline", [(1, 1), (2, 1), (1, -1), (2, -1)])
+def test_table_kinds_agree(gpu_lib, orc, table_kind, inline):
+    """Direct and sparse tables (Sec. 6), with or without inline codes, agree."""
     mih = gpu_lib
     db, qs = workload("lsh", 128, 50_000, 64, seed=5)
     codes, queries = to_dev(db), to_dev(qs)
-    ix = mih.mih_build(codes, 128, 6, table_kind=table_kind)
+    ix = mih.mih_build(codes, 128, 6, table_kind=table_kind, inline_codes=inline)
     info = ix.info()
     assert set(info["table_kind"]) == {table_kind}
+    assert info["inline_codes"] == (1 if inline > 0 else 0)
     assert sum(info["distinct_keys"]) > 0
     want_ids, want_dist = orc.knn(db, qs, 50)
     r = mih.mih_knn(ix, queries, 50)
@@ -101,8 +102,8 @@ def test_mih_work_counters_match_alg3(gpu_lib, orc, kind, q, m, n):
     mih = gpu_lib
     db, qs = workload(kind, q, n, 24, seed=9)
     mo = orc.MihOracle(db, q, m)
-    ix = mih.mih_build(to_dev(db), q, m, scan_factor=-1)     # Alg. 3 exactly, no full pass
-    for k in (1, 25):
+    ixs = [mih.mih_build(to_dev(db), q, m, scan_factor=-1, inline_codes=il) for il in (1, -1)]  # Alg. 3 exactly
+    for k, ix in ((1, ixs[0]), (25, ixs[0]), (25, ixs[1])):
         r = mih.mih_knn(ix, to_dev(qs), k, query_stats=True)
         st = host(r["query_stats"])
         for i in range(len(qs)):
