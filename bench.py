@@ -316,7 +316,8 @@ def run_ours(a):
     # ---- roofline of the dominant kernel (fused MIH search), algorithmic bytes
     sparse = [kd == mih.MIH_TABLE_SPARSE for kd in info["table_kind"]]
     bytes_per_lookup = 8 + (8 if all(sparse) else 0)       # bucket bounds (+ one {key, rank} slot)
-    bytes_per_cand = 4 + q // 8                            # id + full code
+    # full code per candidate; the id too unless the tables keep codes inline
+    bytes_per_cand = q // 8 + (0 if info["inline_codes"] else 4)
     alg_bytes = stats_acc["lookups"] * bytes_per_lookup + stats_acc["candidates_raw"] * bytes_per_cand
     peaks = {}
     try:

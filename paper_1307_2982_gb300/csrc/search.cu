@@ -91,6 +91,33 @@ __device__ __forceinline__ Code<W> load_query(const uint64_t* __restrict__ queri
     return g;
 }
 
+// Substring layout as the kernels see it: for table j, s_mask[j * 2W + i] is
+// the part of 32-bit word i of a code that belongs to substring j, so the
+// substring distance is sum_i popc(x_i & mask) for x = code xor query.  When
+// every substring is one whole 32-bit word (m = 2W, the ALIGNED layout) the
+// substring distances are the per-word popcounts that the full distance sums
+// anyway.
+struct Layout {
+    const int* len;         // s_j
+    const uint32_t* mask;   // [m][2W]
+};
+
+__device__ __forceinline__ void build_layout(const TableDesc* tables, int m, int W, int* s_len, uint32_t* s_mask) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const int off = tables[j].off, len = tables[j].len;
+        s_len[j] = len;
+        for (int i = 0; i < 2 * W; ++i) {
+            const int lo = max(off, 32 * i), hi = min(off + len, 32 * i + 32);
+            uint32_t mk = 0;
+            if (hi > lo) {
+                const int nb = hi - lo, sh = lo - 32 * i;
+                mk = (nb >= 32 ? 0xFFFFFFFFu : ((1u << nb) - 1u)) << sh;
+            }
+            s_mask[j * 2 * W + i] = mk;
+        }
+    }
+}
+
 // Distance of one candidate and its duplicate test.
 //
 // Ring mode (j >= 0): the code was reached at step t = m rho + j and is kept
@@ -100,35 +127,64 @@ __device__ __forceinline__ Code<W> load_query(const uint64_t* __restrict__ queri
 // a kept code enters the histogram and the counters only if its first step is
 // after hist_done (steps up to hist_done were counted before and are revisited
 // only to store their codes under a bound found later).
-template <int W>
-__device__ __forceinline__ void eval_candidate(int m, const int* s_off, const int* s_len, int j, int rho,
-                                               int t_done, int hist_done, const Code<W>& g, const Code<W>& c,
-                                               int& d, bool& keep, bool& count) {
-    Code<W> x;
+template <int W, bool ALIGNED>
+__device__ __forceinline__ void eval_candidate(int m, const Layout& L, int j, int rho, int t_done, int hist_done,
+                                               const Code<W>& g, const Code<W>& c, int& d, bool& keep,
+                                               bool& count) {
+    constexpr int NW = 2 * W;
+    uint32_t x[NW];
 #pragma unroll
-    for (int w = 0; w < W; ++w) x.w[w] = c.w[w] ^ g.w[w];
+    for (int w = 0; w < W; ++w) {
+        const uint64_t v = c.w[w] ^ g.w[w];
+        x[2 * w] = static_cast<uint32_t>(v);
+        x[2 * w + 1] = static_cast<uint32_t>(v >> 32);
+    }
+    int pc[NW];
     d = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) d += __popcll(x.w[w]);
-    if (j >= 0) {
-        keep = true;
-        for (int jj = 0; jj < m; ++jj) {
-            if (jj == j) continue;
-            const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
-            if (jj < j ? (dj <= rho) : (dj < rho)) {
-                keep = false;
-                break;
-            }
+    for (int i = 0; i < NW; ++i) {
+        pc[i] = __popc(x[i]);
+        d += pc[i];
+    }
+    if constexpr (ALIGNED) {
+        if (j >= 0) {
+            keep = true;
+#pragma unroll
+            for (int jj = 0; jj < NW; ++jj)
+                if (jj != j && (jj < j ? (pc[jj] <= rho) : (pc[jj] < rho))) keep = false;
+            count = NW * rho + j > hist_done;
+        } else {
+            int first = 0x7FFFFFFF;
+#pragma unroll
+            for (int jj = 0; jj < NW; ++jj) first = min(first, NW * pc[jj] + jj);
+            keep = first > t_done;
+            count = first > hist_done;
         }
-        count = m * rho + j > hist_done;
     } else {
-        int first = 0x7FFFFFFF;
-        for (int jj = 0; jj < m; ++jj) {
-            const int dj = __popc(substring_bits<W>(x, s_off[jj], s_len[jj]));
-            first = min(first, m * dj + jj);
+        if (j >= 0) {
+            keep = true;
+            for (int jj = 0; jj < m; ++jj) {
+                if (jj == j) continue;
+                int dj = 0;
+#pragma unroll
+                for (int i = 0; i < NW; ++i) dj += __popc(x[i] & L.mask[jj * NW + i]);
+                if (jj < j ? (dj <= rho) : (dj < rho)) {
+                    keep = false;
+                    break;
+                }
+            }
+            count = m * rho + j > hist_done;
+        } else {
+            int first = 0x7FFFFFFF;
+            for (int jj = 0; jj < m; ++jj) {
+                int dj = 0;
+#pragma unroll
+                for (int i = 0; i < NW; ++i) dj += __popc(x[i] & L.mask[jj * NW + i]);
+                first = min(first, m * dj + jj);
+            }
+            keep = first > t_done;
+            count = first > hist_done;
         }
-        keep = first > t_done;
-        count = first > hist_done;
     }
 }
 
@@ -146,8 +202,8 @@ struct CandSource {
 // before any is used, so each lane keeps B gathers in flight.  With inline
 // codes the id is read only for candidates that are stored.  Kept distances
 // go to the warp's shared-memory histogram `whist` (flushed by flush_hist).
-template <int W, int MODE, int B>
-__device__ __forceinline__ void handle_batch(const SearchArgs& a, const int* s_off, const int* s_len,
+template <int W, int MODE, bool ALIGNED, int B>
+__device__ __forceinline__ void handle_batch(const SearchArgs& a, const Layout& L,
                                              uint32_t* whist, uint32_t q, int j, int rho, int t_done, int hist_done,
                                              int bnd, const Code<W>& g, const CandSource& src,
                                              const uint32_t (&pos)[B], const bool (&valid)[B],
@@ -181,7 +237,7 @@ __device__ __forceinline__ void handle_batch(const SearchArgs& a, const int* s_o
     for (int b = 0; b < B; ++b) {
         int d = 0;
         bool keep = false, count = false;
-        if (valid[b]) eval_candidate<W>(a.m, s_off, s_len, j, rho, t_done, hist_done, g, c[b], d, keep, count);
+        if (valid[b]) eval_candidate<W, ALIGNED>(a.m, L, j, rho, t_done, hist_done, g, c[b], d, keep, count);
         if (j < 0) raw_acc += (valid[b] && count) ? 1u : 0u;
         if constexpr (MODE == kModeKnn) {
             if (keep && count) {
@@ -240,8 +296,8 @@ __device__ __forceinline__ void flush_hist(uint32_t* whist, uint32_t* ghist, int
 
 // Warp-cooperative pass over the union of up to 32 buckets [b, b + sz),
 // 32 * B candidates per round.
-template <int W, int MODE, int B>
-__device__ __forceinline__ void scan_buckets(const SearchArgs& a, const int* s_off, const int* s_len,
+template <int W, int MODE, bool ALIGNED, int B>
+__device__ __forceinline__ void scan_buckets(const SearchArgs& a, const Layout& L,
                                              uint32_t* whist, const CandSource& src, uint32_t q, int j,
                                              int rho, int hist_done, int bnd, const Code<W>& g, uint32_t b,
                                              uint32_t sz, uint32_t& unique_acc) {
@@ -267,8 +323,8 @@ __device__ __forceinline__ void scan_buckets(const SearchArgs& a, const int* s_o
             pos[k] = valid[k] ? ob + (idx - oe) : 0u;
         }
         uint32_t unused = 0;
-        handle_batch<W, MODE, B>(a, s_off, s_len, whist, q, j, rho, -1, hist_done, bnd, g, src, pos, valid,
-                                 unique_acc, unused);
+        handle_batch<W, MODE, ALIGNED, B>(a, L, whist, q, j, rho, -1, hist_done, bnd, g, src, pos, valid,
+                                          unique_acc, unused);
     }
 }
 
@@ -277,17 +333,17 @@ constexpr int kBigBatch = 8;   // candidates in flight per lane, big-bucket slic
 constexpr int kWarps = kSearchThreads / 32;
 constexpr int kHistBins = 257; // distances 0..256
 
-template <int W, int MODE>
+template <int W, int MODE, bool ALIGNED>
 __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
     __shared__ int s_off[kMaxTables];
     __shared__ int s_len[kMaxTables];
+    __shared__ uint32_t s_mask[kMaxTables * 2 * W];
     __shared__ uint32_t s_hist[kWarps][kHistBins];
-    for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
-        s_off[j] = a.tables[j].off;
-        s_len[j] = a.tables[j].len;
-    }
+    for (int j = threadIdx.x; j < a.m; j += blockDim.x) s_off[j] = a.tables[j].off;
+    build_layout(a.tables, a.m, W, s_len, s_mask);
     for (int i = threadIdx.x; i < kWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     __syncthreads();
+    const Layout L{s_len, s_mask};
     const uint32_t lane = lane_id();
     uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned long long total_chunks = a.chunk_off[a.nq];
@@ -324,8 +380,8 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
                     valid[k] = i < end;
                     pos[k] = static_cast<uint32_t>(i);
                 }
-                handle_batch<W, MODE, kBigBatch>(a, s_off, s_len, whist, q, -1, 0, t - 1, hd, bnd, g, src, pos,
-                                                 valid, unique, raw);
+                handle_batch<W, MODE, ALIGNED, kBigBatch>(a, L, whist, q, -1, 0, t - 1, hd, bnd, g, src, pos,
+                                                          valid, unique, raw);
             }
             if (MODE == kModeKnn) flush_hist(whist, ghist, a.q);
 #pragma unroll
@@ -384,7 +440,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
             }
             raw += sz;
             if (__any_sync(0xFFFFFFFFu, sz != 0))
-                scan_buckets<W, MODE, kBatch>(a, s_off, s_len, whist, src, q, j, rho, hd, bnd, g, b, sz, unique);
+                scan_buckets<W, MODE, ALIGNED, kBatch>(a, L, whist, src, q, j, rho, hd, bnd, g, b, sz, unique);
         }
         if (MODE == kModeKnn) flush_hist(whist, ghist, a.q);
         // per-query counters (lookups, raw candidates, unique candidates) of
@@ -407,17 +463,15 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
 }
 
 // Slices of large buckets, one warp per slice, 32 * kBigBatch entries per round.
-template <int W, int MODE>
+template <int W, int MODE, bool ALIGNED>
 __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a) {
-    __shared__ int s_off[kMaxTables];
     __shared__ int s_len[kMaxTables];
+    __shared__ uint32_t s_mask[kMaxTables * 2 * W];
     __shared__ uint32_t s_hist[kWarps][kHistBins];
-    for (int j = threadIdx.x; j < a.m; j += blockDim.x) {
-        s_off[j] = a.tables[j].off;
-        s_len[j] = a.tables[j].len;
-    }
+    build_layout(a.tables, a.m, W, s_len, s_mask);
     for (int i = threadIdx.x; i < kWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     __syncthreads();
+    const Layout L{s_len, s_mask};
     const uint32_t lane = lane_id();
     uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned int count = min(*a.big_count, a.big_cap);
@@ -444,8 +498,8 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
                 valid[k] = e < bs.end;
                 pos[k] = e;
             }
-            handle_batch<W, MODE, kBigBatch>(a, s_off, s_len, whist, bs.q, j, rho, -1, hd, bnd, g, src, pos, valid,
-                                             unique, unused);
+            handle_batch<W, MODE, ALIGNED, kBigBatch>(a, L, whist, bs.q, j, rho, -1, hd, bnd, g, src, pos, valid,
+                                                      unique, unused);
         }
         if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(bs.q) * (a.q + 1), a.q);
 #pragma unroll
@@ -754,19 +808,30 @@ unsigned grid1(uint64_t n) {
     return static_cast<unsigned>(g ? g : 1);
 }
 
-template <int W, int MODE>
-mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s) {
-    static int bps = 0;  // resident blocks per SM (same on every GB300)
+// Persistent grids: as many CTAs as fit on the GPU at once.
+template <int W, int MODE, bool ALIGNED>
+mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s) {
+    static int bps = 0, bps_big = 0;  // resident blocks per SM (same on every GB300)
     if (bps == 0) {
-        int v = 0;
-        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE>, kSearchThreads, 0));
+        int v = 0, w = 0;
+        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE, ALIGNED>, kSearchThreads, 0));
+        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, search_big_kernel<W, MODE, ALIGNED>, kSearchThreads,
+                                                               0));
+        bps_big = w > 0 ? w : 1;
         bps = v > 0 ? v : 1;
     }
-    search_kernel<W, MODE><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
+    search_kernel<W, MODE, ALIGNED><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
     MIH_LAUNCH_CHECK();
-    search_big_kernel<W, MODE><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
+    search_big_kernel<W, MODE, ALIGNED><<<dev.sms * bps_big, kSearchThreads, 0, s>>>(a);
     MIH_LAUNCH_CHECK();
     return MIH_OK;
+}
+
+template <int W, int MODE>
+mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s) {
+    // every substring is one whole 32-bit word exactly when m = 2W
+    if (a.m == 2 * W) return launch_search_wa<W, MODE, true>(a, dev, s);
+    return launch_search_wa<W, MODE, false>(a, dev, s);
 }
 
 template <int MODE>
