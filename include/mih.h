@@ -200,6 +200,37 @@ MIH_API mih_status linscan_knn(const uint64_t *codes, uint64_t n, int q, const u
                        void *stream);
 
 /* ------------------------------------------------------------------------
+ * linscan_knn_noalloc -- linscan_knn for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a service of the library.
+ *
+ * Some callers must not call cudaMalloc or cudaFree while they search: a
+ * process whose memory allocator has already reserved (nearly) all device
+ * memory, so a fresh allocation fails; a latency-bound serving thread, where
+ * cudaFree (and often cudaMalloc) synchronises the whole device and stalls
+ * the work of other streams; code held to a fixed device-memory budget.
+ * This entry point allocates nothing.  Its scratch is one array of about
+ * 16.3 MiB compiled into the library (a static __device__ array), which every
+ * GPU that loads the library holds until the process exits.  The caller
+ * still passes the inputs and the outputs.
+ *
+ * Results equal linscan_knn's with a uniform k (out_ids / out_dist hold
+ * nq * k entries).  Limits: nq <= 256 and 1 <= k <= 256, else MIH_EINVAL;
+ * when ties at the k-th distance need more than 2^20 second-pass slots in
+ * one call it returns MIH_ENOMEM (use linscan_knn then).
+ * Set-up: the first call on each device looks up the array's device address
+ * with cudaGetSymbolAddress (that device current); make this first call on a
+ * device before capturing any stream.
+ * Concurrency: all calls on a device share the one array, and each call clears
+ * what must start at zero when it begins; calls that overlap on the GPU (from
+ * other streams or host threads) race and corrupt each other's results.
+ * Synchronises `stream`.
+ * Errors: MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EINTERNAL.
+ */
+MIH_API mih_status linscan_knn_noalloc(const uint64_t *codes, uint64_t n, int q,
+                                       const uint64_t *queries, uint32_t nq, uint32_t k,
+                                       uint32_t *out_ids, int32_t *out_dist, void *stream);
+
+/* ------------------------------------------------------------------------
  * Host-only helpers (no GPU needed).
  */
 

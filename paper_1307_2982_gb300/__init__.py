@@ -28,7 +28,7 @@ PAD_ID = 0xFFFFFFFF
 EXPORTS = (
     "mih_build", "mih_free", "mih_index_get_info", "mih_knn", "mih_rnear", "linscan_knn",
     "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
-    "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile",
+    "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
 )
 
 
@@ -107,6 +107,8 @@ def load():
     lib.mih_last_error.restype = ctypes.c_char_p
     lib.mih_version.argtypes = []
     lib.mih_version.restype = ctypes.c_char_p
+    lib.linscan_knn_noalloc.argtypes = [P, u64, i32, P, u32, u32, P, P, P]
+    lib.linscan_knn_noalloc.restype = st
     lib.mih_set_timing.argtypes = [i32]
     lib.mih_set_timing.restype = None
     lib.mih_last_profile.argtypes = [P]
@@ -322,3 +324,23 @@ def linscan_knn(codes, q: int, queries, k, stream=None, out=None):
     if off is not None:
         res["offsets"] = off
     return res
+
+
+def linscan_knn_noalloc(codes, q: int, queries, k: int, stream=None, out=None):
+    """linscan_knn with a uniform k that allocates no device memory (nq, k <= 256).
+
+    For callers that cannot allocate during a search; the library's fixed
+    scratch array is shared by all calls on a device, so calls must not
+    overlap on the GPU."""
+    import torch
+
+    cptr, n = _codes_arg(codes, q)
+    qptr, nq = _codes_arg(queries, q)
+    if out is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+        dist = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    else:
+        ids, dist = out
+    _check(load().linscan_knn_noalloc(cptr, n, q, qptr, nq, k, _ptr(ids), _ptr(dist), _stream(stream)),
+           "linscan_knn_noalloc")
+    return {"ids": ids, "dist": dist}

@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "launch.h"
@@ -439,5 +440,220 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
     si.out_dist = out_dist;
     MIH_TRY(launch_select(si, ws));
     MIH_CUDA(cudaStreamSynchronize(s));
+    return MIH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// linscan_knn_noalloc: the same linear scan with all scratch memory in one
+// fixed array inside the library, for callers that must not allocate device
+// memory during a search (see include/mih.h).  The array lives in device
+// memory of every GPU that loads the library until the process exits.
+namespace mih {
+namespace {
+
+constexpr uint32_t kNaMaxQueries = 256;        // queries per call
+constexpr uint32_t kNaMaxK = 256;              // k per call
+constexpr uint32_t kNaCap = 4096;              // first-pass slots per query
+constexpr uint64_t kNaSecond = 1ull << 20;     // second-pass slots per call
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+constexpr size_t kNaThr = 0;
+constexpr size_t kNaDk = na_align(kNaThr + 4 * kNaMaxQueries);
+constexpr size_t kNaCnt = na_align(kNaDk + 4 * kNaMaxQueries);
+constexpr size_t kNaCursor = na_align(kNaCnt + 4 * kNaMaxQueries);
+constexpr size_t kNaFlags = na_align(kNaCursor + 4 * kNaMaxQueries);   // n_over, scan error, select error
+constexpr size_t kNaNeed = na_align(kNaFlags + 16);
+constexpr size_t kNaHist = na_align(kNaNeed + 8 * (kNaMaxQueries + 1));
+constexpr size_t kNaBuf = na_align(kNaHist + 4ull * kNaMaxQueries * 257);
+constexpr size_t kNaBuf2 = na_align(kNaBuf + 8ull * kNaMaxQueries * kNaCap);
+constexpr size_t kNaBytes = na_align(kNaBuf2 + 8ull * kNaSecond);   // about 16.3 MiB
+
+static __device__ __align__(256) unsigned char g_linscan_scratch[kNaBytes];
+
+std::mutex g_na_mu;
+void* g_na_addr[64] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of a __device__ array is not its address).
+mih_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    MIH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d out of range", dev);
+        return MIH_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_linscan_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            set_error("linscan_knn_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return MIH_ECUDA;
+        }
+        g_na_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_na_addr[dev]);
+    return MIH_OK;
+}
+
+}  // namespace
+}  // namespace mih
+
+extern "C" mih_status linscan_knn_noalloc(const uint64_t* codes, uint64_t n, int q, const uint64_t* queries,
+                                          uint32_t nq, uint32_t k, uint32_t* out_ids, int32_t* out_dist,
+                                          void* stream) {
+    using namespace mih;
+    clear_error();
+    if (q != 64 && q != 128 && q != 256) {
+        set_error("linscan_knn_noalloc: q must be 64, 128 or 256 (got %d)", q);
+        return MIH_EINVAL;
+    }
+    if (n >= 0xFFFFFFFFull) {
+        set_error("linscan_knn_noalloc: n must be below 2^32 - 1");
+        return MIH_EINVAL;
+    }
+    if (nq > kNaMaxQueries) {
+        set_error("linscan_knn_noalloc: at most %u queries per call (got %u)", kNaMaxQueries, nq);
+        return MIH_EINVAL;
+    }
+    if (k < 1 || k > kNaMaxK) {
+        set_error("linscan_knn_noalloc: k must be in [1, %u] (got %u)", kNaMaxK, k);
+        return MIH_EINVAL;
+    }
+    if (nq == 0) return MIH_OK;
+    MIH_TRY(check_device_ptr(queries, "queries"));
+    MIH_TRY(check_device_ptr(out_ids, "out_ids"));
+    MIH_TRY(check_device_ptr(out_dist, "out_dist"));
+    if (n > 0) {
+        MIH_TRY(check_device_ptr(codes, "codes"));
+        MIH_TRY(check_code_alignment(codes, q / 64, "codes"));
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* base = nullptr;
+    MIH_TRY(noalloc_scratch(&base));
+    DeviceInfo dev;
+    MIH_TRY(device_info(&dev));
+    const int W = q / 64;
+    int32_t* thr = reinterpret_cast<int32_t*>(base + kNaThr);
+    int32_t* dk = reinterpret_cast<int32_t*>(base + kNaDk);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(base + kNaCnt);
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(base + kNaCursor);
+    unsigned int* n_over = reinterpret_cast<unsigned int*>(base + kNaFlags);
+    int* scan_err = reinterpret_cast<int*>(base + kNaFlags + 4);
+    int* select_err = reinterpret_cast<int*>(base + kNaFlags + 8);
+    uint64_t* need = reinterpret_cast<uint64_t*>(base + kNaNeed);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + kNaHist);
+    uint64_t* buf = reinterpret_cast<uint64_t*>(base + kNaBuf);
+    uint64_t* buf2 = reinterpret_cast<uint64_t*>(base + kNaBuf2);
+
+    // The array keeps the previous call's contents: clear what must start at zero.
+    MIH_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * nq * (q + 1), s));
+    MIH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * nq, s));
+    MIH_CUDA(cudaMemsetAsync(cursor, 0, sizeof(uint32_t) * nq, s));
+    MIH_CUDA(cudaMemsetAsync(base + kNaFlags, 0, 16, s));
+    MIH_CUDA(cudaMemsetAsync(need, 0, sizeof(uint64_t) * (nq + 1), s));
+
+    bool second = false;
+    if (n > 0) {
+        const uint64_t S = std::min<uint64_t>(n, kSampleMax);
+        if (W == 1) MIH_TRY(launch_sample<1>(codes, S, queries, nq, q, nullptr, k, n, thr, s));
+        else if (W == 2) MIH_TRY(launch_sample<2>(codes, S, queries, nq, q, nullptr, k, n, thr, s));
+        else MIH_TRY(launch_sample<4>(codes, S, queries, nq, q, nullptr, k, n, thr, s));
+        int32_t hthr[kNaMaxQueries];
+        MIH_CUDA(cudaMemcpyAsync(hthr, thr, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        std::nth_element(hthr, hthr + nq / 2, hthr + nq);
+        const int G = choose_group(W, hthr[nq / 2]);
+
+        const uint32_t qtiles = (nq + kLsQueries - 1) / kLsQueries;
+        uint64_t splits = (static_cast<uint64_t>(dev.sms) * 4 + qtiles - 1) / qtiles;
+        const uint64_t max_splits = (n + kLsTile - 1) / kLsTile;
+        if (splits > max_splits) splits = max_splits;
+        if (splits < 1) splits = 1;
+        if (splits > 65535) splits = 65535;
+        uint64_t split_len = (n + splits - 1) / splits;
+        split_len = (split_len + kLsTile - 1) / kLsTile * kLsTile;
+        splits = (n + split_len - 1) / split_len;
+
+        ScanArgs a;
+        memset(&a, 0, sizeof(a));
+        a.codes = codes;
+        a.n = n;
+        a.queries = queries;
+        a.nq = nq;
+        a.qbits = q;
+        a.kq = nullptr;
+        a.k_uniform = k;
+        a.split_len = split_len;
+        a.thr = thr;
+        a.hist = hist;
+        a.buf = buf;
+        a.cap = kNaCap;
+        a.cnt = cnt;
+        const dim3 grid(qtiles, static_cast<unsigned>(splits));
+        MIH_TRY(launch_scan(a, W, G, grid, s));
+        finish_first_pass_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, q, n, nullptr, k, hist, cnt, kNaCap, dk, thr,
+                                                              need, n_over);
+        MIH_LAUNCH_CHECK();
+        unsigned int hover = 0;
+        MIH_CUDA(cudaMemcpyAsync(&hover, n_over, sizeof(hover), cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        if (hover > 0) {
+            // Offsets of the second pass (exact counts within d_k), on the host.
+            uint64_t h[kNaMaxQueries + 1];
+            MIH_CUDA(cudaMemcpyAsync(h, need, sizeof(uint64_t) * (nq + 1), cudaMemcpyDeviceToHost, s));
+            MIH_CUDA(cudaStreamSynchronize(s));
+            uint64_t run = 0;
+            for (uint32_t i = 0; i <= nq; ++i) {
+                const uint64_t c = i < nq ? h[i] : 0;
+                h[i] = run;
+                run += c;
+            }
+            if (run > kNaSecond) {
+                set_error("linscan_knn_noalloc: %llu codes tie within the k-th distance; the fixed scratch holds "
+                          "%llu (use linscan_knn)",
+                          static_cast<unsigned long long>(run), static_cast<unsigned long long>(kNaSecond));
+                return MIH_ENOMEM;
+            }
+            MIH_CUDA(cudaMemcpyAsync(need, h, sizeof(uint64_t) * (nq + 1), cudaMemcpyHostToDevice, s));
+            ScanArgs b = a;
+            b.buf = buf2;
+            b.cnt = cursor;
+            b.base = need;
+            b.second_pass = 1;
+            b.err = scan_err;
+            MIH_TRY(launch_scan(b, W, 1, grid, s));
+            second = true;
+        }
+    } else {
+        MIH_CUDA(cudaMemsetAsync(dk, 0, sizeof(int32_t) * nq, s));
+    }
+
+    SelectInputs si;
+    si.nq = nq;
+    si.n = n;
+    si.q = q;
+    si.kq = nullptr;
+    si.k_uniform = k;
+    si.kmax = k;
+    si.out_off = nullptr;
+    si.hist = hist;
+    si.dk = dk;
+    si.buf1 = buf;
+    si.cap = kNaCap;
+    si.cnt1 = cnt;
+    si.buf2 = second ? buf2 : nullptr;
+    si.base2 = need;
+    si.out_ids = out_ids;
+    si.out_dist = out_dist;
+    MIH_TRY(launch_select_noalloc(si, select_err, s));
+    int herr[2] = {0, 0};
+    MIH_CUDA(cudaMemcpyAsync(herr, scan_err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    if (herr[0] || herr[1]) {
+        set_error("linscan_knn_noalloc: internal count mismatch (scan %d, select %d)", herr[0], herr[1]);
+        return MIH_EINTERNAL;
+    }
     return MIH_OK;
 }

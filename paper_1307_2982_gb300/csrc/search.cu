@@ -1013,6 +1013,40 @@ mih_status launch_select(const SelectInputs& in, Workspace& ws) {
     return MIH_OK;
 }
 
+// Selection with a caller-provided error flag (zeroed by the caller); no
+// allocation.  Only for min(kmax, n) <= 6144 (48 KB of shared memory).
+mih_status launch_select_noalloc(const SelectInputs& in, int* err, cudaStream_t s) {
+    if (in.nq == 0) return MIH_OK;
+    uint32_t P = 1;
+    const uint64_t kk_max = std::min<uint64_t>(in.kmax, in.n);
+    while (P < kk_max) P <<= 1;
+    const size_t smem = static_cast<size_t>(P) * sizeof(uint64_t);
+    if (smem > 48 * 1024) {
+        set_error("select: k too large for the fixed-scratch path");
+        return MIH_EINVAL;
+    }
+    SelectArgs a;
+    a.nq = in.nq;
+    a.n = in.n;
+    a.q = in.q;
+    a.kq = in.kq;
+    a.k_uniform = in.k_uniform;
+    a.out_off = in.out_off;
+    a.hist = in.hist;
+    a.dk = in.dk;
+    a.buf1 = in.buf1;
+    a.cap = in.cap;
+    a.cnt1 = in.cnt1;
+    a.buf2 = in.buf2;
+    a.base2 = in.base2;
+    a.out_ids = in.out_ids;
+    a.out_dist = in.out_dist;
+    a.err = err;
+    select_kernel<<<in.nq, 256, smem, s>>>(a);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
 uint32_t knn_buffer_cap(uint32_t kmax) {
     uint64_t c = 16ull * kmax;
     if (c < 4096) c = 4096;

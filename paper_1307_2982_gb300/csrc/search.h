@@ -34,6 +34,10 @@ struct SelectInputs {
 
 mih_status launch_select(const SelectInputs& in, Workspace& ws);
 
+// The same selection writing a failure into `err` (device int, zeroed by the
+// caller) instead of allocating a flag; for min(kmax, n) <= 6144.
+mih_status launch_select_noalloc(const SelectInputs& in, int* err, cudaStream_t s);
+
 // Validate k (uniform or per query, device) and the output pointers; *kmax
 // receives the largest k.
 mih_status check_k_args(uint32_t nq, const uint32_t* k, uint32_t k_uniform, const uint64_t* out_offsets,
