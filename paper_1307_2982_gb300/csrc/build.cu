@@ -190,7 +190,9 @@ mih_status build_table(mih_index* ix, int j, int kind, const DeviceInfo& dev, cu
     t.codes = nullptr;
     if (ix->inline_codes && n > 0) {
         uint64_t* inl;
-        MIH_TRY(index_alloc(ix, reinterpret_cast<void**>(&inl), n * ix->W * sizeof(uint64_t)));
+        // 16 bytes of padding: streamed copies of 8-byte codes are widened to
+        // 16-byte boundaries and may read one code past the end
+        MIH_TRY(index_alloc(ix, reinterpret_cast<void**>(&inl), n * ix->W * sizeof(uint64_t) + 16));
         if (ix->W == 1) gather_codes_kernel<1><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, inl);
         else if (ix->W == 2) gather_codes_kernel<2><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, inl);
         else gather_codes_kernel<4><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, inl);

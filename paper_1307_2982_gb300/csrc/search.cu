@@ -74,6 +74,8 @@ struct SearchArgs {
     const uint8_t* exh;                // per query: verify every code this launch
     const int32_t* hist_done;          // knn: last step already in the histogram (-1: none)
     uint64_t n;
+    int inline_codes;                  // tables keep codes in bucket order
+    int* timeout;                      // set when a bounded wait gives up
 };
 
 // Chunks of step t for a query: ceil(C(s_j, rho) / 256), 0 if rho > s_j.
@@ -197,6 +199,13 @@ struct CandSource {
     bool by_id;             // codes are indexed by id: load the id first
 };
 
+template <int W, int MODE, bool ALIGNED, int B>
+__device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout& L, uint32_t* whist, uint32_t q,
+                                               int j, int rho, int t_done, int hist_done, int bnd, const Code<W>& g,
+                                               const CandSource& src, const uint32_t (&pos)[B],
+                                               const bool (&valid)[B], const Code<W> (&c)[B],
+                                               const uint32_t (&id)[B], uint32_t& unique_acc, uint32_t& raw_acc);
+
 // B candidates per lane, warp-synchronous (all 32 lanes call together; every
 // valid candidate belongs to query q).  All B loads of a kind are issued
 // before any is used, so each lane keeps B gathers in flight.  With inline
@@ -230,6 +239,19 @@ __device__ __forceinline__ void handle_batch(const SearchArgs& a, const Layout& 
                 for (int w = 0; w < W; ++w) c[b].w[w] = 0ull;
         }
     }
+    process_loaded<W, MODE, ALIGNED, B>(a, L, whist, q, j, rho, t_done, hist_done, bnd, g, src, pos, valid, c, id,
+                                        unique_acc, raw_acc);
+}
+
+// The second half of handle_batch, for codes already in registers (from
+// global memory or from a shared-memory stage).  id[b] is the candidate's id
+// unless the source keeps codes inline (then ids are read only when stored).
+template <int W, int MODE, bool ALIGNED, int B>
+__device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout& L, uint32_t* whist, uint32_t q,
+                                               int j, int rho, int t_done, int hist_done, int bnd, const Code<W>& g,
+                                               const CandSource& src, const uint32_t (&pos)[B],
+                                               const bool (&valid)[B], const Code<W> (&c)[B],
+                                               const uint32_t (&id)[B], uint32_t& unique_acc, uint32_t& raw_acc) {
     const bool lazy_id = !src.by_id && src.ids != nullptr;
     const uint32_t lane = lane_id();
     const uint32_t lt = (1u << lane) - 1u;
@@ -507,6 +529,192 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
         if (lane == 0 && a.qstats) atomicAdd(&a.qstats[4ull * bs.q + 2], static_cast<unsigned long long>(unique));
     }
 }
+
+// ------------------------------------------------------- streamed slices
+// With inline codes every big-bucket slice is one contiguous run of codes.
+// Each warp streams its slices through two 4 KB shared-memory stages: lane 0
+// starts a bulk asynchronous copy (cp.async.bulk, completion counted on an
+// mbarrier) of the next stage while the warp verifies the current one.  Every
+// wait on an mbarrier is bounded; on expiry the kernel raises a.timeout,
+// waits (bounded) for its own copies still in flight and leaves.
+constexpr uint32_t kStageBytes = 4096;
+constexpr int kStreamWarps = 8;
+constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kStageSlot = kStageBytes + 16;   // + one 8-byte code of realignment (W = 1)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// One stage: entries [pos, pos + cnt) of a slice ending at `end`, all of
+// query q at step t.  Warp-uniform.
+struct Stage {
+    uint32_t q;
+    int t;
+    uint32_t pos, cnt, end;
+    bool valid;
+};
+
+template <int W>
+__device__ __forceinline__ Stage next_stage(const SearchArgs& a, const Stage& st, unsigned int count) {
+    constexpr uint32_t kPer = kStageBytes / (8 * W);
+    Stage r = st;
+    if (!st.valid) return r;
+    if (st.pos + st.cnt < st.end) {
+        r.pos = st.pos + st.cnt;
+        r.cnt = min(kPer, st.end - r.pos);
+        return r;
+    }
+    for (;;) {
+        unsigned int i = 0;
+        if (lane_id() == 0) i = atomicAdd(a.big_next, 1u);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        if (i >= count) {
+            r.valid = false;
+            return r;
+        }
+        const BigSlice bs = a.big[i];
+        if (bs.q == kPadId) continue;
+        r.q = bs.q;
+        r.t = bs.t;
+        r.pos = bs.begin;
+        r.end = bs.end;
+        r.cnt = min(kPer, bs.end - bs.begin);
+        return r;
+    }
+}
+
+// Lane 0 starts the copy of stage st into slot `buf`; returns the code offset
+// of the stage inside the slot (nonzero only when W = 1 realigns to 16 bytes).
+template <int W>
+__device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage& st, unsigned char* buf,
+                                                uint64_t* bar) {
+    const uint64_t* codes = a.tables[st.t % a.m].codes;
+    uint32_t lo = st.pos, shift = 0, bytes = st.cnt * 8u * W;
+    if constexpr (W == 1) {
+        lo = st.pos & ~1u;
+        shift = st.pos - lo;
+        bytes = ((st.cnt + shift) * 8u + 15u) & ~15u;   // the table keeps 16 bytes of padding
+    }
+    if (lane_id() == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads of the slot are done
+        bulk_copy_to_smem(buf, codes + static_cast<uint64_t>(lo) * W, bytes, bar);
+    }
+    return shift;
+}
+
+template <int W, int MODE, bool ALIGNED>
+__global__ void __launch_bounds__(kStreamWarps * 32) search_stream_kernel(SearchArgs a) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ int s_len[kMaxTables];
+    __shared__ uint32_t s_mask[kMaxTables * 2 * W];
+    __shared__ uint32_t s_hist[kStreamWarps][kHistBins];
+    __shared__ __align__(8) uint64_t s_bar[kStreamWarps][2];
+    build_layout(a.tables, a.m, W, s_len, s_mask);
+    for (int i = threadIdx.x; i < kStreamWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    if (lane == 0) {
+        mbar_init(&s_bar[warp][0], 1);
+        mbar_init(&s_bar[warp][1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const Layout L{s_len, s_mask};
+    uint32_t* whist = s_hist[warp];
+    unsigned char* slot[2] = {dsm + (2 * warp) * kStageSlot, dsm + (2 * warp + 1) * kStageSlot};
+    uint64_t* bar[2] = {&s_bar[warp][0], &s_bar[warp][1]};
+    uint32_t parity[2] = {0u, 0u};
+    uint32_t shift[2] = {0u, 0u};
+    const unsigned int count = min(*a.big_count, a.big_cap);
+
+    Stage none;
+    none.valid = true;
+    none.pos = none.cnt = none.end = 0;
+    none.q = 0;
+    none.t = 0;
+    Stage cur = next_stage<W>(a, none, count);
+    if (!cur.valid) return;
+    shift[0] = issue_stage<W>(a, cur, slot[0], bar[0]);
+    Stage nxt = next_stage<W>(a, cur, count);
+    if (nxt.valid) shift[1] = issue_stage<W>(a, nxt, slot[1], bar[1]);
+    int b = 0;
+    while (cur.valid) {
+        if (!mbar_wait_bounded(bar[b], parity[b])) {
+            if (lane == 0) atomicExch(a.timeout, 1);
+            if (nxt.valid) mbar_wait_bounded(bar[b ^ 1], parity[b ^ 1]);   // let our other copy land
+            return;
+        }
+        parity[b] ^= 1u;
+        // verify the stage out of shared memory
+        const int j = cur.t % a.m, rho = cur.t / a.m;
+        const Code<W> g = load_query<W>(a.queries, cur.q);
+        const TableDesc& tab = a.tables[j];
+        const CandSource src{tab.codes, tab.ids, false};
+        const int hd = a.hist_done ? __ldg(a.hist_done + cur.q) : -1;
+        const int bnd = __ldg(a.bound + cur.q);
+        const Code<W>* sc = reinterpret_cast<const Code<W>*>(slot[b]) + shift[b];
+        uint32_t unique = 0, unused = 0;
+        constexpr int B = 4;
+        for (uint32_t base = 0; base < cur.cnt; base += 32 * B) {
+            uint32_t pos[B], id[B];
+            bool valid[B];
+            Code<W> c[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const uint32_t i = base + k * 32 + lane;
+                valid[k] = i < cur.cnt;
+                pos[k] = cur.pos + i;
+                id[k] = pos[k];
+                if (valid[k]) c[k] = sc[i];
+                else
+#pragma unroll
+                    for (int w = 0; w < W; ++w) c[k].w[w] = 0ull;
+            }
+            process_loaded<W, MODE, ALIGNED, B>(a, L, whist, cur.q, j, rho, -1, hd, bnd, g, src, pos, valid, c, id,
+                                                unique, unused);
+        }
+        if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(cur.q) * (a.q + 1), a.q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
+        if (lane == 0 && a.qstats) atomicAdd(&a.qstats[4ull * cur.q + 2], static_cast<unsigned long long>(unique));
+        __syncwarp();
+        // the slot just read takes the stage after next
+        const Stage nn = next_stage<W>(a, nxt, count);
+        if (nn.valid) shift[b] = issue_stage<W>(a, nn, slot[b], bar[b]);
+        cur = nxt;
+        nxt = nn;
+        b ^= 1;
+    }
+}
+
+size_t stream_smem_bytes() { return static_cast<size_t>(kStreamWarps) * 2 * kStageSlot; }
 
 // ------------------------------------------------------------ planning
 // Chunk count of each query's step range [t_lo, t_hi].
@@ -822,7 +1030,21 @@ mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStre
     }
     search_kernel<W, MODE, ALIGNED><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
     MIH_LAUNCH_CHECK();
-    search_big_kernel<W, MODE, ALIGNED><<<dev.sms * bps_big, kSearchThreads, 0, s>>>(a);
+    if (a.inline_codes) {
+        static int bps_stream = 0;
+        const size_t smem = stream_smem_bytes();
+        if (bps_stream == 0) {
+            MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+            int v = 0;
+            MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_stream_kernel<W, MODE, ALIGNED>,
+                                                                   kStreamWarps * 32, smem));
+            bps_stream = v > 0 ? v : 1;
+        }
+        search_stream_kernel<W, MODE, ALIGNED><<<dev.sms * bps_stream, kStreamWarps * 32, smem, s>>>(a);
+    } else {
+        search_big_kernel<W, MODE, ALIGNED><<<dev.sms * bps_big, kSearchThreads, 0, s>>>(a);
+    }
     MIH_LAUNCH_CHECK();
     return MIH_OK;
 }
@@ -847,6 +1069,7 @@ struct Plan {
     unsigned long long* counters = nullptr;  // [0] chunk_next; [1] big_count|big_next (as uint32 x2)
     BigSlice* big = nullptr;
     uint32_t big_cap = 0;
+    int* timeout = nullptr;                  // raised by a bounded wait that gave up
 };
 
 mih_status plan_alloc(Plan& p, uint32_t nq, Workspace& ws) {
@@ -854,6 +1077,20 @@ mih_status plan_alloc(Plan& p, uint32_t nq, Workspace& ws) {
     MIH_TRY(ws.alloc(&p.counters, 2));
     p.big_cap = 1u << 20;
     MIH_TRY(ws.alloc(&p.big, p.big_cap));
+    MIH_TRY(ws.alloc(&p.timeout, 1));
+    MIH_CUDA(cudaMemsetAsync(p.timeout, 0, sizeof(int), ws.stream()));
+    return MIH_OK;
+}
+
+// MIH_ETIMEOUT if a kernel of this call gave up a bounded wait (syncs).
+mih_status check_timeout(const Plan& p, cudaStream_t s) {
+    int h = 0;
+    MIH_CUDA(cudaMemcpyAsync(&h, p.timeout, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        set_error("a bounded wait on a bulk copy expired");
+        return MIH_ETIMEOUT;
+    }
     return MIH_OK;
 }
 
@@ -875,6 +1112,8 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
     a.big_cap = p.big_cap;
     a.big_count = reinterpret_cast<unsigned int*>(p.counters + 1);
     a.big_next = a.big_count + 1;
+    a.inline_codes = ix->inline_codes ? 1 : 0;
+    a.timeout = p.timeout;
     main_kernel_begin(s);
     const mih_status st = launch_search<MODE>(a, ix->W, dev, s);
     main_kernel_end(s);
@@ -1136,7 +1375,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
             MIH_LAUNCH_CHECK();
             unsigned int hact = 0;
             MIH_CUDA(cudaMemcpyAsync(&hact, active, sizeof(hact), cudaMemcpyDeviceToHost, s));
-            MIH_CUDA(cudaStreamSynchronize(s));
+            MIH_TRY(check_timeout(plan, s));
             if (hact == 0) break;
             if (t == qb) {
                 set_error("mih_knn: queries still active after q steps");
@@ -1179,6 +1418,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         b.err = err;
         MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
         ++waves;
+        MIH_TRY(check_timeout(plan, s));
         MIH_TRY(check_flag(err, "mih_knn: second pass found more codes within d_k than counted", s));
     }
 
@@ -1287,6 +1527,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
         init_range_kernel<<<grid1(nq), 256, 0, s>>>(nq, 0, reff, reff, t_lo, t_hi, bound);
         MIH_LAUNCH_CHECK();
         MIH_TRY(run_wave<kModeCount>(ix, a, plan, t_lo, t_hi, dev, ws));
+        MIH_TRY(check_timeout(plan, s));
     }
     // CSR offsets of the results: exclusive scan of the counts, last = total
     uint64_t* off64;
@@ -1343,6 +1584,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
         b.qstats = nullptr;
         b.err = err;
         MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
+        MIH_TRY(check_timeout(plan, s));
         MIH_TRY(check_flag(err, "mih_rnear: fill pass found more results than the count pass", s));
         int qbits = 1;
         while ((1u << qbits) < nq) ++qbits;

@@ -228,3 +228,33 @@ def test_edge_cases(gpu_lib, orc):
     h = ctypes.c_void_p()
     hostbuf = torch.zeros((10, 2), dtype=torch.int64)
     assert lib.mih_build(mih._ptr(hostbuf), 10, 128, 4, None, None, ctypes.byref(h)) == mih.MIH_EINVAL
+
+
+@pytest.mark.parametrize("q", [64, 128, 256])
+def test_big_buckets_streamed_and_gathered(gpu_lib, orc, q):
+    """Buckets far above the slice threshold, with and without inline codes.
+
+    20 patterns repeated 2500 times each (plus random codes), shuffled, so
+    every substring of a pattern indexes a bucket of >= 2500 entries that
+    starts at arbitrary (also odd) positions."""
+    mih = gpu_lib
+    rng = np.random.default_rng(77)
+    pats = synth.uniform_codes(20, q, 70)
+    db = np.concatenate([np.repeat(pats, 2500, axis=0), synth.uniform_codes(10_001, q, 71)])
+    db = db[rng.permutation(len(db))]
+    qs = np.concatenate([perturb(pats[:6], 2, 72), synth.uniform_codes(4, q, 73)])
+    codes, queries = to_dev(db), to_dev(qs)
+    W = q // 64
+    for m in sorted({2 * W, 2 * W + 1}):
+        for inline in (1, -1):
+            ix = mih.mih_build(codes, q, m, inline_codes=inline)
+            assert max(ix.info()["max_bucket"]) >= 2500
+            for k in (10, 3000):
+                want_ids, want_dist = orc.knn(db, qs, k)
+                r = mih.mih_knn(ix, queries, k)
+                assert np.array_equal(ids_of(r["ids"]), want_ids), (m, inline, k)
+                assert np.array_equal(host(r["dist"]), want_dist), (m, inline, k)
+            woff, wid, wd = orc.rnear(db, qs, 3)
+            got = mih.mih_rnear(ix, queries, 3)
+            assert np.array_equal(ids_of(got["ids"]), wid) and np.array_equal(host(got["dist"]), wd)
+            ix.free()
