@@ -85,7 +85,10 @@ typedef struct {
 typedef struct {
     uint64_t lookups;            /* buckets examined (Sec. 3, "lookups") */
     uint64_t candidates_raw;     /* bucket entries read */
-    uint64_t candidates_unique;  /* candidates left after duplicate removal */
+    uint64_t candidates_unique;  /* candidates left after duplicate removal; counted
+                                    only when query_stats is requested (else 0): without
+                                    it candidates beyond a query's bound are dropped
+                                    before the duplicate test */
     uint64_t steps;              /* Alg. 3 steps executed, summed over queries */
     uint64_t phase2_queries;     /* k-NN queries re-collected in a second pass */
     uint64_t waves;              /* search waves launched */
@@ -149,6 +152,8 @@ MIH_API mih_status mih_index_get_info(const mih_index *index, mih_index_info *in
  * query_stats  device uint64[nq][4] or NULL: per query lookups, raw
  *              candidates, unique candidates, last step executed.  In the
  *              paper's stopping rule the last step equals the k-th distance.
+ *              Requesting it makes every candidate pass the duplicate test
+ *              (slower); results are the same either way.
  * stats        host, nullable: aggregate counters of this call.
  * Every k must satisfy 1 <= k <= MIH_MAX_K.  Synchronises `stream`.
  * Step t searches ring floor(t/m) of table (t mod m); a query stops after

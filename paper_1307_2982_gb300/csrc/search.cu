@@ -76,6 +76,7 @@ struct SearchArgs {
     uint64_t n;
     int inline_codes;                  // tables keep codes in bucket order
     int* timeout;                      // set when a bounded wait gives up
+    int exact_stats;                   // count every unique candidate (per-query counters requested)
 };
 
 // Chunks of step t for a query: ceil(C(s_j, rho) / 256), 0 if rho > s_j.
@@ -122,6 +123,12 @@ __device__ __forceinline__ void build_layout(const TableDesc* tables, int m, int
 
 // Distance of one candidate and its duplicate test.
 //
+// A candidate farther than `far` is dropped right after its distance: with a
+// bound U on the k-th distance (far = U) such a code is never stored, and
+// every later stop test only counts distances below the step index, which
+// stays below U while the query runs.  far is "no limit" while the query has
+// no bound yet and when exact per-query counters were requested.
+//
 // Ring mode (j >= 0): the code was reached at step t = m rho + j and is kept
 // only if t is its first step (no table j' < j within rho bits, none j' > j
 // within rho - 1).  Full-pass mode (j < 0): every code is visited once and
@@ -131,7 +138,7 @@ __device__ __forceinline__ void build_layout(const TableDesc* tables, int m, int
 // only to store their codes under a bound found later).
 template <int W, bool ALIGNED>
 __device__ __forceinline__ void eval_candidate(int m, const Layout& L, int j, int rho, int t_done, int hist_done,
-                                               const Code<W>& g, const Code<W>& c, int& d, bool& keep,
+                                               int far, const Code<W>& g, const Code<W>& c, int& d, bool& keep,
                                                bool& count) {
     constexpr int NW = 2 * W;
     uint32_t x[NW];
@@ -147,6 +154,11 @@ __device__ __forceinline__ void eval_candidate(int m, const Layout& L, int j, in
     for (int i = 0; i < NW; ++i) {
         pc[i] = __popc(x[i]);
         d += pc[i];
+    }
+    if (d > far) {
+        // beyond the query's bound: never stored and never inside a stop test
+        keep = count = false;
+        return;
     }
     if constexpr (ALIGNED) {
         if (j >= 0) {
@@ -253,13 +265,14 @@ __device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout
                                                const bool (&valid)[B], const Code<W> (&c)[B],
                                                const uint32_t (&id)[B], uint32_t& unique_acc, uint32_t& raw_acc) {
     const bool lazy_id = !src.by_id && src.ids != nullptr;
+    const int far = (bnd < 0 || a.exact_stats) ? 0x7FFFFFFF : bnd;
     const uint32_t lane = lane_id();
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         int d = 0;
         bool keep = false, count = false;
-        if (valid[b]) eval_candidate<W, ALIGNED>(a.m, L, j, rho, t_done, hist_done, g, c[b], d, keep, count);
+        if (valid[b]) eval_candidate<W, ALIGNED>(a.m, L, j, rho, t_done, hist_done, far, g, c[b], d, keep, count);
         if (j < 0) raw_acc += (valid[b] && count) ? 1u : 0u;
         if constexpr (MODE == kModeKnn) {
             if (keep && count) {
@@ -1362,6 +1375,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     a.exh = exh;
     a.hist_done = hist_done;
     a.n = ix->n;
+    a.exact_stats = query_stats != nullptr ? 1 : 0;
 
     uint64_t waves = 0;
     if (ix->n > 0) {
@@ -1450,7 +1464,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         for (uint32_t i = 0; i < nq; ++i) {
             stats->lookups += h[4ull * i];
             stats->candidates_raw += h[4ull * i + 1];
-            stats->candidates_unique += h[4ull * i + 2];
+            stats->candidates_unique += query_stats ? h[4ull * i + 2] : 0;
             stats->steps += ix->n > 0 ? h[4ull * i + 3] + 1 : 0;
         }
         stats->phase2_queries = hover;
@@ -1509,6 +1523,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
     a.cnt = cnt;
     a.qstats = qstats;
     a.n = ix->n;
+    a.exact_stats = query_stats != nullptr ? 1 : 0;
     uint8_t* exh;
     MIH_TRY(ws.alloc(&exh, nqa));
     {
@@ -1552,7 +1567,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
             for (uint32_t i = 0; i < nq; ++i) {
                 stats->lookups += h[4ull * i];
                 stats->candidates_raw += h[4ull * i + 1];
-                stats->candidates_unique += h[4ull * i + 2];
+                stats->candidates_unique += query_stats ? h[4ull * i + 2] : 0;
                 stats->steps += ix->n > 0 ? static_cast<uint64_t>(reff) + 1 : 0;
             }
             stats->waves = ix->n > 0 ? 1 : 0;
