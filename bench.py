@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=32, help="queries timed on the CPU oracle")
     ap.add_argument("--no-linscan", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--probe", type=int, default=0, help="bound-probe entries per bucket (0 default, <0 off)")
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -257,7 +258,7 @@ def run_ours(a):
     # index build (Algorithm 1), timed on the device
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    index = mih.mih_build(codes, q, m)
+    index = mih.mih_build(codes, q, m, probe=a.probe)
     ev1.record()
     torch.cuda.synchronize()
     build_ms = ev0.elapsed_time(ev1)

@@ -78,7 +78,11 @@ typedef struct {
                               candidates are one contiguous read.  0 = auto (when
                               ids and inline codes fit in 60% of the free
                               device memory), 1 = always, negative = never. */
-    int32_t reserved[13];  /* must be zero */
+    int32_t probe;         /* Before the first step, measure up to `probe` entries
+                              of each query's own bucket in every table to get a
+                              first bound on its k-th distance (results
+                              unchanged).  0 = default (1024), negative = off. */
+    int32_t reserved[12];  /* must be zero */
 } mih_params;
 
 /* Aggregate work counters of one mih_knn / mih_rnear call (host struct). */

@@ -40,7 +40,7 @@ class MihError(RuntimeError):
 
 class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
-                ("inline_codes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 13)]
+                ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("reserved", ctypes.c_int32 * 12)]
 
 
 class mih_stats(ctypes.Structure):
@@ -224,12 +224,13 @@ class MihIndex:
 
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
-              inline_codes: int = 0, stream=None) -> MihIndex:
+              inline_codes: int = 0, probe: int = 0, stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
     p.scan_factor = scan_factor
     p.inline_codes = inline_codes
+    p.probe = probe
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)

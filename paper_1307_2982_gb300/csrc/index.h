@@ -21,4 +21,5 @@ struct mih_index {
     uint64_t bytes = 0;                         // device bytes owned
     int scan_factor = 0;                        // lookup budget factor (see mih_params)
     bool inline_codes = false;                  // tables hold codes in bucket order
+    int probe = 1024;                           // bound-probe entries per bucket (0 = off)
 };

@@ -14,7 +14,7 @@ constexpr uint32_t kPadId = 0xFFFFFFFFu;
 constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
 constexpr int kChunkKeys = 256;          // ring keys per work chunk (one warp)
 constexpr int kKeysPerLane = kChunkKeys / 32;
-constexpr uint32_t kBigBucket = 2048;    // buckets above this go to the big list
+constexpr uint32_t kBigBucket = 64;      // buckets above this go to the slice list
 
 // ---------------------------------------------------------------- tables
 // One substring hash table (Sec. 6): either direct-addressed CSR offsets over

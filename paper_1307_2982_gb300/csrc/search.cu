@@ -12,8 +12,10 @@
 // (combinatorial number system) and walks 8 keys by Gosper steps, looks the
 // buckets up, and the warp then shares out the union of the 32 buckets'
 // entries, verifies each candidate on the full code and bins it by
-// distance.  Buckets above 2048 entries are cut into slices that a second
-// kernel spreads over all warps.
+// distance.  Buckets above 64 entries are cut into slices of at most 1024
+// that a second kernel spreads over all warps (streamed through shared memory
+// when the tables keep their codes inline).  Before the first step a probe
+// of each query's own buckets gives a first bound on its k-th distance.
 //
 // Duplicates (Sec. 6 "Duplicate Candidates") are removed without an n-bit
 // set: a code reached at step t = m rho + j is kept only if t is the first
@@ -799,7 +801,7 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
                 bound[q] = first_reach;
                 t_lo[q] = 0;                // revisit steps 0..t to store under the new bound
             } else {
-                if (first_reach >= 0) bound[q] = first_reach;
+                if (first_reach >= 0 && (bound[q] < 0 || first_reach < bound[q])) bound[q] = first_reach;
                 t_lo[q] = t + 1;
             }
             t_hi[q] = t + 1;
@@ -988,6 +990,67 @@ __global__ void init_knn_kernel(uint32_t nq, uint64_t n, int32_t* t_lo, int32_t*
     }
 }
 
+// A first bound on each query's k-th distance, before any step runs: one warp
+// per query measures up to `probe` entries of the query's own bucket in every
+// table (the buckets of its first m steps).  Any min(k, n) codes of the
+// database bound the k-th distance from above, so the smallest D with at
+// least min(k, n) probed codes within D is a valid bound; queries that probe
+// fewer codes keep bound = -1 (histogram-only steps until one exists).
+
+template <int W>
+__global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __restrict__ tables, int m, int qbits,
+                                                          const uint64_t* __restrict__ codes,
+                                                          const uint64_t* __restrict__ queries, uint32_t nq,
+                                                          uint64_t n, const uint32_t* __restrict__ kq,
+                                                          uint32_t k_uniform, uint32_t probe,
+                                                          int32_t* __restrict__ bound) {
+    __shared__ uint32_t s_hist[8][kHistBins];
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    uint32_t* h = s_hist[warp];
+    for (int d = lane; d <= qbits; d += 32) h[d] = 0;
+    __syncwarp();
+    const uint32_t q = blockIdx.x * 8 + warp;
+    if (q >= nq) return;
+    const Code<W> g = load_query<W>(queries, q);
+    for (int j = 0; j < m; ++j) {
+        const TableDesc& t = tables[j];
+        uint32_t b = 0, e = 0;
+        if (lane == 0) lookup_bucket(t, substring_bits<W>(g, t.off, t.len), b, e);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        e = __shfl_sync(0xFFFFFFFFu, e, 0);
+        const uint32_t end = min(e, b + probe);
+        for (uint32_t p = b + lane; p < end; p += 32) {
+            const Code<W> c = t.codes ? load_code<W>(t.codes, p) : load_code<W>(codes, __ldg(t.ids + p));
+            // a code also filed under the query's key in an earlier table is
+            // counted there or not at all: the count never exceeds the number
+            // of distinct codes, so the bound stays valid
+            Code<W> x;
+#pragma unroll
+            for (int w = 0; w < W; ++w) x.w[w] = c.w[w] ^ g.w[w];
+            bool first = true;
+            for (int jj = 0; jj < j && first; ++jj)
+                if (substring_bits<W>(x, tables[jj].off, tables[jj].len) == 0u) first = false;
+            if (first) atomicAdd(&h[hamming<W>(c, g)], 1u);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const uint64_t kv = kq ? kq[q] : k_uniform;
+        const uint32_t kk = static_cast<uint32_t>(kv < n ? kv : n);
+        uint32_t cum = 0;
+        int bnd = -1;
+        for (int d = 0; d <= qbits; ++d) {
+            cum += h[d];
+            if (cum >= kk) {
+                bnd = d;
+                break;
+            }
+        }
+        bound[q] = bnd;
+    }
+}
+
 __global__ void init_range_kernel(uint32_t nq, int32_t lo, int32_t hi, int32_t bnd, int32_t* t_lo, int32_t* t_hi,
                                   int32_t* bound) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -1088,7 +1151,7 @@ struct Plan {
 mih_status plan_alloc(Plan& p, uint32_t nq, Workspace& ws) {
     MIH_TRY(ws.alloc(&p.chunk_off, static_cast<size_t>(nq) + 1));
     MIH_TRY(ws.alloc(&p.counters, 2));
-    p.big_cap = 1u << 20;
+    p.big_cap = 1u << 22;
     MIH_TRY(ws.alloc(&p.big, p.big_cap));
     MIH_TRY(ws.alloc(&p.timeout, 1));
     MIH_CUDA(cudaMemsetAsync(p.timeout, 0, sizeof(int), ws.stream()));
@@ -1299,9 +1362,12 @@ mih_status launch_select_noalloc(const SelectInputs& in, int* err, cudaStream_t 
     return MIH_OK;
 }
 
-uint32_t knn_buffer_cap(uint32_t kmax) {
+uint32_t knn_buffer_cap(uint32_t kmax, uint32_t nq) {
     uint64_t c = 16ull * kmax;
-    if (c < 4096) c = 4096;
+    if (c < 16384) c = 16384;
+    // at most 2 GiB of buffers per call, but never below 4096 slots
+    const uint64_t mem_cap = (1ull << 31) / (8ull * (nq > 0 ? nq : 1));
+    if (c > mem_cap) c = mem_cap < 4096 ? 4096 : mem_cap;
     if (c > 65536) c = 65536;
     return static_cast<uint32_t>(c);
 }
@@ -1328,7 +1394,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     DeviceInfo dev;
     MIH_TRY(device_info(&dev));
     const int qb = ix->q;
-    const uint32_t cap = knn_buffer_cap(kmax);
+    const uint32_t cap = knn_buffer_cap(kmax, nq);
 
     int32_t *t_lo, *t_hi, *bound, *dk;
     uint32_t *hist, *cnt1;
@@ -1355,6 +1421,21 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_TRY(ws.alloc(&hist_done, nq));
     init_knn_kernel<<<grid1(nq), 256, 0, s>>>(nq, ix->n, t_lo, t_hi, bound, dk, hist_done);
     MIH_LAUNCH_CHECK();
+    if (ix->n > 0 && query_stats == nullptr && ix->probe > 0) {
+        // (with per-query counters requested the steps run exactly as Alg. 3
+        // counts them, from a histogram-only start)
+        const unsigned blocks = (nq + 7) / 8;
+        if (ix->W == 1)
+            bound_probe_kernel<1><<<blocks, 256, 0, s>>>(ix->dev_tables, ix->m, qb, ix->codes, queries, nq, ix->n, k,
+                                                         k_uniform, static_cast<uint32_t>(ix->probe), bound);
+        else if (ix->W == 2)
+            bound_probe_kernel<2><<<blocks, 256, 0, s>>>(ix->dev_tables, ix->m, qb, ix->codes, queries, nq, ix->n, k,
+                                                         k_uniform, static_cast<uint32_t>(ix->probe), bound);
+        else
+            bound_probe_kernel<4><<<blocks, 256, 0, s>>>(ix->dev_tables, ix->m, qb, ix->codes, queries, nq, ix->n, k,
+                                                         k_uniform, static_cast<uint32_t>(ix->probe), bound);
+        MIH_LAUNCH_CHECK();
+    }
     Plan plan;
     MIH_TRY(plan_alloc(plan, nq, ws));
 

@@ -43,7 +43,8 @@ mih_status launch_select_noalloc(const SelectInputs& in, int* err, cudaStream_t 
 mih_status check_k_args(uint32_t nq, const uint32_t* k, uint32_t k_uniform, const uint64_t* out_offsets,
                         const uint32_t* out_ids, const int32_t* out_dist, uint32_t* kmax, Workspace& ws);
 
-// Slots of the bounded per-query candidate buffer for a given largest k.
-uint32_t knn_buffer_cap(uint32_t kmax);
+// Slots of the bounded per-query candidate buffer for a given largest k and
+// batch size.
+uint32_t knn_buffer_cap(uint32_t kmax, uint32_t nq);
 
 }  // namespace mih
