@@ -54,7 +54,7 @@ WORKLOAD_NAMES = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="H", choices=sorted(WORKLOADS))
@@ -108,7 +108,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -160,6 +160,39 @@ def per_query_k(nq, k, seed_shift=0):
 
     if k == "kper":
         return synth.per_query_k(nq, seed=3 + seed_shift, kmax=1000)
+    return None
+
+
+def source_sha256() -> str:
+    """Hash of the kernel sources (csrc/* and include/mih.h), as in profiles/."""
+    import glob
+    import hashlib
+
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1307_2982_gb300", "csrc", "*")))
+    files.append(os.path.join(ROOT, "include", "mih.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_ratio():
+    """DRAM bytes per algorithmic byte of the search kernels, from the committed
+    ncu summary, if the kernels have not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "search_kernels_5e7x128_traffic.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if "=" in line and line.split("=")[0].strip() in ("traffic_per_algorithmic_byte", "source_sha256"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") == source_sha256():
+            return float(kv["traffic_per_algorithmic_byte"])
+    except (OSError, ValueError, KeyError):
+        pass
     return None
 
 
@@ -276,17 +309,17 @@ def run_ours(a):
     def step():
         return mih.mih_knn(index, queries, karg, out=(out_ids, out_dist))
 
+    sampler = ClockSampler(local)
+    sampler.start()                       # clocks sampled from the warm-up through the timed region
     for _ in range(a.warmup):
         r = step()
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, device time, max over ranks
     mih.mih_set_timing(True)
-    sampler = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats_acc = {"lookups": 0, "candidates_raw": 0, "candidates_unique": 0, "steps": 0, "phase2_queries": 0,
                  "waves": 0}
@@ -329,9 +362,13 @@ def run_ours(a):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = (alg_bytes / max(main_launches, 1)) / ((main_ms / max(main_launches, 1)) / 1000.0) / 1e9 \
         if main_ms > 0 else None
+    ratio = traffic_ratio() if (q == 128 and kind == "lsh") else None
+    traffic = ratio * alg_bytes / max(main_launches, 1) if ratio else None
     roofline = {"bound": "hbm", "kernel": "search_kernel+search_big_kernel (fused MIH search)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                "traffic_source": ("profiles/search_kernels_5e7x128_traffic.txt: dram bytes per algorithmic byte "
+                                   "on the 5e7 case, scaled to this launch") if traffic else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "per_launch_ms": main_ms / max(main_launches, 1), "launches_per_step": main_launches / a.steps,
                 "search_share_of_step": main_ms / ms if ms > 0 else None,
