@@ -34,6 +34,8 @@ if ROOT not in sys.path:
 
 METRIC = "exact 100-NN queries/s on 1B×128-bit codes, MIH vs linear scan on GB300; p99 ms"
 
+# candidate m for the autotuner (substrings of at most 32 bits)
+AUTOTUNE_M = {"H": [4, 5], "1": [3, 4, 5], "2": [5, 6, 7], "3": [2, 3, 4], "4": [8, 9, 10]}
 # workload name -> (kind, n, q, nq, k, m); "kper" = per-query log-uniform k
 WORKLOADS = {
     "H": ("lsh", 1_000_000_000, 128, 10_000, 100, 4),
@@ -66,6 +68,7 @@ def parse():
     ap.add_argument("--no-linscan", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--probe", type=int, default=0, help="bound-probe entries per bucket (0 default, <0 off)")
+    ap.add_argument("--no-autotune", action="store_true", help="use the workload's default m")
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -288,6 +291,18 @@ def run_ours(a):
     torch.cuda.empty_cache()      # hand the generator's cached blocks back before the build
     gen_s = time.perf_counter() - t0
 
+    # m by the library's autotuner on 1000 hold-out queries (Sec. 6), unless --m is given
+    tune = None
+    if not a.no_autotune and a.m is None:
+        hold = make_codes(kind, 1000, q, 5, dev)
+        kk_tune = k if k != "kper" else 100
+        t0 = time.perf_counter()
+        m, tune_ms = mih.mih_autotune(codes, q, hold, kk_tune, candidates=AUTOTUNE_M[a.workload], probe=a.probe)
+        tune = {"candidates": AUTOTUNE_M[a.workload], "ms_per_query": {str(kq): v for kq, v in tune_ms.items()},
+                "chosen_m": m, "holdout_queries": 1000, "k": kk_tune, "seconds": time.perf_counter() - t0}
+        del hold
+        torch.cuda.empty_cache()
+
     # index build (Algorithm 1), timed on the device
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
@@ -453,7 +468,8 @@ def run_ours(a):
                    "k": k if k != "kper" else "log-uniform[1,1000]", "m": m, "codes": kind,
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (codes + tables, no flush)",
                    "substring_bits": info["substring_length"], "table_kind": info["table_kind"],
-                   "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s},
+                   "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s,
+                   "inline_codes": info["inline_codes"], "autotune": tune},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "mih_stats_per_step": {kk: v / a.steps for kk, v in stats_acc.items()},
         "linscan": linscan, "parity": parity,

@@ -209,6 +209,33 @@ MIH_API mih_status linscan_knn(const uint64_t *codes, uint64_t n, int q, const u
                        void *stream);
 
 /* ------------------------------------------------------------------------
+ * mih_autotune -- choose the number of substrings m by timing the search on
+ * a hold-out set of queries (Sec. 6 "Number of Substrings": estimate the
+ * run time for m near q / log2(n) and keep the fastest; Table 4).
+ *
+ * codes, n, q   as in mih_build (device, borrowed only during the call).
+ * queries, nq   device, hold-out queries (1 <= nq <= 2^23).
+ * k             1 <= k <= MIH_MAX_K.
+ * candidates    host int[n_candidates] values of m to try, or NULL to try
+ *               mih_suggest_m(q, n) and its neighbours (invalid values are
+ *               skipped: m < 1, m > q or substrings above 32 bits).
+ * params        host, nullable: build parameters used for every candidate.
+ * best_m        host out: the fastest m.
+ * ms_per_query  host out, nullable: double[n_candidates] (3 when
+ *               candidates is NULL): mean search time per query of each
+ *               candidate, -1 for skipped ones.
+ * Each candidate builds an index, runs one untimed and one timed mih_knn
+ * over the hold-out queries, and frees the index, so at most one index
+ * exists at a time.  Synchronises `stream`.
+ * Errors: MIH_EINVAL (no valid candidate, sizes), then as mih_build and
+ * mih_knn.
+ */
+MIH_API mih_status mih_autotune(const uint64_t *codes, uint64_t n, int q, const uint64_t *queries,
+                                uint32_t nq, uint32_t k, const int *candidates, int n_candidates,
+                                const mih_params *params, void *stream, int *best_m,
+                                double *ms_per_query);
+
+/* ------------------------------------------------------------------------
  * linscan_knn_noalloc -- linscan_knn for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a service of the library.
  *

@@ -29,6 +29,7 @@ EXPORTS = (
     "mih_build", "mih_free", "mih_index_get_info", "mih_knn", "mih_rnear", "linscan_knn",
     "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
+    "mih_autotune",
 )
 
 
@@ -107,6 +108,8 @@ def load():
     lib.mih_last_error.restype = ctypes.c_char_p
     lib.mih_version.argtypes = []
     lib.mih_version.restype = ctypes.c_char_p
+    lib.mih_autotune.argtypes = [P, u64, i32, P, u32, u32, P, i32, P, P, ctypes.POINTER(i32), P]
+    lib.mih_autotune.restype = st
     lib.linscan_knn_noalloc.argtypes = [P, u64, i32, P, u32, u32, P, P, P]
     lib.linscan_knn_noalloc.restype = st
     lib.mih_set_timing.argtypes = [i32]
@@ -234,6 +237,23 @@ def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_fact
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)
+
+
+def mih_autotune(codes, q: int, queries, k: int, candidates=None, stream=None, **build):
+    """Pick m by timing mih_knn on hold-out queries (Sec. 6).  Returns (best_m, {m: ms per query})."""
+    cptr, n = _codes_arg(codes, q)
+    qptr, nq = _codes_arg(queries, q)
+    p = mih_params()
+    for key, v in build.items():
+        setattr(p, key, v)
+    cand = None if candidates is None else (ctypes.c_int * len(candidates))(*candidates)
+    ncand = 3 if candidates is None else len(candidates)
+    times = (ctypes.c_double * ncand)()
+    best = ctypes.c_int(0)
+    _check(load().mih_autotune(cptr, n, q, qptr, nq, k, cand, ncand if candidates else 0, ctypes.byref(p),
+                               _stream(stream), ctypes.byref(best), times), "mih_autotune")
+    ms = list(candidates) if candidates else [mih_suggest_m(q, n) + d for d in (-1, 0, 1)]
+    return best.value, {m: t for m, t in zip(ms, times) if t >= 0}
 
 
 def mih_free(index: MihIndex):

@@ -258,3 +258,19 @@ def test_big_buckets_streamed_and_gathered(gpu_lib, orc, q):
             got = mih.mih_rnear(ix, queries, 3)
             assert np.array_equal(ids_of(got["ids"]), wid) and np.array_equal(host(got["dist"]), wd)
             ix.free()
+
+
+def test_autotune_picks_a_candidate(gpu_lib, orc):
+    """Sec. 6: m chosen by timing the search on hold-out queries."""
+    mih = gpu_lib
+    db, _ = workload("lsh", 128, 200_000, 1)
+    hold = synth.lsh_codes(300, 128, 9)
+    best, times = mih.mih_autotune(to_dev(db), 128, to_dev(hold), 20, candidates=[3, 4, 5, 6])
+    assert best in (4, 5, 6) and set(times) == {4, 5, 6}          # m = 3 needs 43-bit substrings: skipped
+    assert all(t > 0 for t in times.values()) and times[best] == min(times.values())
+    best2, times2 = mih.mih_autotune(to_dev(db), 128, to_dev(hold), 20)    # around q / log2(n) = 7.2
+    assert best2 in times2 and set(times2) == {6, 7, 8}
+    ix = mih.mih_build(to_dev(db), 128, best)
+    want_ids, want_dist = orc.knn(db, hold[:50], 20)
+    r = mih.mih_knn(ix, to_dev(hold[:50]), 20)
+    assert np.array_equal(ids_of(r["ids"]), want_ids) and np.array_equal(host(r["dist"]), want_dist)
