@@ -43,6 +43,7 @@ WORKLOADS = {
     "2": ("lsh", 10_000_000, 128, 10_000, 100, 6),
     "3": ("uniform", 1_000_000_000, 64, 10_000, "kper", 2),
     "4": ("lsh", 1_000_000_000, 256, 10_000, "kper", 9),
+    "5": ("serve", 1_000_000_000, 128, 0, "kper", 4),
 }
 WORKLOAD_NAMES = {
     "H": "1B x 128-bit LSH-style codes, 10k queries, k=100",
@@ -50,6 +51,7 @@ WORKLOAD_NAMES = {
     "2": "10M x 128-bit LSH-style codes, 10k queries, k=100",
     "3": "1B x 64-bit uniform codes, 10k queries, k log-uniform [1,1000]",
     "4": "1B x 256-bit LSH-style codes, 10k queries, k log-uniform [1,1000]",
+    "5": "serving: 1M x 64 uniform + 100M x 128 LSH + 1B x 128 LSH, Poisson, k log-uniform [1,1000]",
 }
 
 
@@ -69,6 +71,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--probe", type=int, default=0, help="bound-probe entries per bucket (0 default, <0 off)")
     ap.add_argument("--no-autotune", action="store_true", help="use the workload's default m")
+    ap.add_argument("--serve-qps", type=float, default=200_000.0, help="offered load of the serving check")
+    ap.add_argument("--no-serve", action="store_true")
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -438,6 +442,23 @@ def run_ours(a):
                    "identical_to_mih": same, "pairs_per_s": pairs / (ls_ms / 1000.0),
                    "scan_kernel_ms": lprof["main_ms"]}
 
+    # ---- serving: Poisson k=100 requests against the resident index (p50/p99)
+    serve = None
+    if not a.no_serve and kq_np is None:
+        from paper_1307_2982_gb300 import serving, synth
+
+        nreq = int(a.serve_qps * 1.0)
+        gen = (lambda d, c, sd: synth.lsh_codes(c, q, sd)) if kind == "lsh" else \
+            (lambda d, c, sd: synth.uniform_codes(c, q, sd))
+        req = serving.poisson_requests(nreq, a.serve_qps, [q], k_max=1, seed=4, query_gen=gen)
+        req.k[:] = k
+        srv = serving.MihServer([index], result_budget=256 << 20, max_batch=8192)
+        srv.run(serving.Requests(req.arrival[:2000] * 0.01, req.db[:2000], req.k[:2000], req.codes[:2000]))  # warm
+        res = srv.run(req)
+        serve = res.summary()
+        serve.update({"offered_qps": a.serve_qps, "k": k, "db": workload_name(a).split(",")[0],
+                      "latency": "arrival to results in host memory, continuous batching"})
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1) + sampled parity
     cpu = None
     parity = None
@@ -472,7 +493,7 @@ def run_ours(a):
                    "inline_codes": info["inline_codes"], "autotune": tune},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "mih_stats_per_step": {kk: v / a.steps for kk, v in stats_acc.items()},
-        "linscan": linscan, "parity": parity,
+        "linscan": linscan, "parity": parity, "serving": serve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -481,10 +502,58 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_serving(a):
+    """Three resident databases, Poisson requests at three offered loads."""
+    import torch
+
+    import paper_1307_2982_gb300 as mih
+    from paper_1307_2982_gb300 import serving, synth
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mih.load()
+    specs = [("uniform", 1_000_000, 64), ("lsh", 100_000_000, 128), ("lsh", a.n or 1_000_000_000, 128)]
+    dbs, idx = [], []
+    for kind, n, q in specs:
+        codes = make_codes(kind, n, q, 0, dev)
+        torch.cuda.empty_cache()
+        m = mih.mih_suggest_m(q, n)
+        idx.append(mih.mih_build(codes, q, m, probe=a.probe))
+        dbs.append({"codes": kind, "n": n, "q": q, "m": m, "index_bytes": idx[-1].info()["index_bytes"]})
+
+    def gen(d, c, sd):
+        kind, n, q = specs[d]
+        return synth.uniform_codes(c, q, sd) if kind == "uniform" else synth.lsh_codes(c, q, sd)
+
+    loads = []
+    srv = serving.MihServer(idx, result_budget=512 << 20, max_batch=8192)
+    warm = serving.poisson_requests(3000, 100_000.0, [q for _, _, q in specs], seed=9, query_gen=gen)
+    srv.run(warm)
+    for rate in (10_000.0, 100_000.0, 1_000_000.0):
+        nreq = int(min(rate * 2.0, 2_000_000))
+        req = serving.poisson_requests(nreq, rate, [q for _, _, q in specs], seed=4, query_gen=gen)
+        res = srv.run(req)
+        s = res.summary()
+        s["offered_qps"] = rate
+        loads.append(s)
+    best = max(l["throughput_qps"] for l in loads)
+    line = {"metric": "served exact k-NN queries/s (three resident databases); p99 ms", "value": best,
+            "unit": "queries/s", "n_gpus": 1, "steps": len(loads), "warmup": 1, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAMES["5"], "databases": dbs,
+                                            "k": "log-uniform[1,1000]", "result_budget_bytes": 512 << 20,
+                                            "max_batch": 8192, "workers_per_db": 2},
+            "loads": loads}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "5":
+        run_serving(a)
     else:
         run_ours(a)
 
