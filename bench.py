@@ -285,8 +285,11 @@ def run_ours(a):
     # inputs: the whole database on every rank, this rank's own queries
     t0 = time.perf_counter()
     codes = make_codes(kind, n, q, 0, dev)
+    from paper_1307_2982_gb300 import replicas
+
     all_q = make_codes(kind, nq * world, q, 1, dev)
-    queries = all_q[rank * nq:(rank + 1) * nq].contiguous()
+    lo, hi = replicas.shard(nq * world, world, rank)      # this rank's queries (weak scaling)
+    queries = all_q[lo:hi].contiguous()
     del all_q
     kq_np = per_query_k(nq, k, seed_shift=rank)
     kt = torch.from_numpy(kq_np.astype(np.int32)).to(dev) if kq_np is not None else None
@@ -358,11 +361,7 @@ def run_ours(a):
         dist.barrier()
     clocks = sampler.stop()
     mih.mih_set_timing(False)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), device=dev)
     ms_per_step = ms / a.steps
     value = world * nq * a.steps / (ms / 1000.0)
 
@@ -411,11 +410,7 @@ def run_ours(a):
         dist_h.copy_(out_dist, non_blocking=True)
     f1.record()
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replicas.max_over_ranks(f0.elapsed_time(f1), device=dev)
     e2e = {"value": world * nq * a.steps / (e2e_ms / 1000.0), "unit": "queries/s",
            "h2d_bytes_per_step": int(qh.numel() * 8),
            "d2h_bytes_per_step": int((ids_h.numel() + dist_h.numel()) * 4)}
