@@ -31,8 +31,7 @@ namespace mih {
 namespace {
 
 constexpr int kLsThreads = 256;
-constexpr int kLsCodesPerThread = 4;                       // J
-constexpr int kLsTile = kLsThreads * kLsCodesPerThread;    // codes per tile
+constexpr int kLsTile = kLsThreads * 8;                    // codes per tile (split granularity)
 constexpr int kLsQueries = 64;                             // queries per CTA
 constexpr int kLsRefresh = 8;                              // tiles between bound refreshes
 constexpr uint32_t kSampleMax = 1u << 18;                  // prefix sample for the first bound
@@ -61,43 +60,56 @@ __device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform
     return static_cast<uint32_t>(k < n ? k : n);
 }
 
-// Lower bound on popcount(x) from ORs of G consecutive 32-bit words.
-template <int W, int G>
-__device__ __forceinline__ int or_bound(const uint64_t (&x)[W]) {
-    if constexpr (G == 1) {
-        int d = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) d += __popcll(x[w]);
-        return d;
-    } else if constexpr (G == 2) {
-        int d = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w)
-            d += __popc(static_cast<uint32_t>(x[w]) | static_cast<uint32_t>(x[w] >> 32));
-        return d;
-    } else {
-        constexpr int per = G / 2;  // 64-bit words per group
-        int d = 0;
-#pragma unroll
-        for (int grp = 0; grp < W / per; ++grp) {
-            uint64_t o = 0;
-#pragma unroll
-            for (int w = 0; w < per; ++w) o |= x[grp * per + w];
-            d += __popc(static_cast<uint32_t>(o) | static_cast<uint32_t>(o >> 32));
-        }
-        return d;
-    }
+// (a ^ b) | c in one LOP3 (truth table 0xBE over inputs 0xF0, 0xCC, 0xAA).
+__device__ __forceinline__ uint32_t xor_or(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("lop3.b32 %0, %1, %2, %3, 0xBE;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
 }
+
+// Lower bound on the distance from ORs of G consecutive 32-bit words of
+// code ^ query (G = 1: the exact distance).  Words are 32-bit halves,
+// little-endian, so the chain folds the xor into each OR step.
+template <int NW, int G>
+__device__ __forceinline__ int or_bound32(const uint32_t (&c)[NW], const uint32_t (&g)[NW]) {
+    int d = 0;
+    if constexpr (G == 1) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) d += __popc(c[i] ^ g[i]);
+    } else {
+#pragma unroll
+        for (int grp = 0; grp < NW / G; ++grp) {
+            uint32_t t = c[grp * G + G - 1] ^ g[grp * G + G - 1];
+#pragma unroll
+            for (int i = G - 2; i >= 0; --i) t = xor_or(c[grp * G + i], g[grp * G + i], t);
+            d += __popc(t);
+        }
+    }
+    return d;
+}
+
+template <int W>
+struct ScanShape {
+    static constexpr int J = W <= 2 ? 8 : 4;   // codes per thread per tile
+};
 
 template <int W, int G>
 __global__ void __launch_bounds__(kLsThreads) linscan_kernel(ScanArgs a) {
-    __shared__ uint64_t s_q[kLsQueries][W];
+    constexpr int NW = 2 * W;
+    constexpr int J = ScanShape<W>::J;
+    constexpr int kTile = kLsThreads * J;
+    __shared__ uint32_t s_q[kLsQueries][NW];
     __shared__ int s_thr[kLsQueries];
     const uint32_t q0 = blockIdx.x * kLsQueries;
     const uint32_t nql = min(static_cast<uint32_t>(kLsQueries), a.nq - q0);
-    for (int i = threadIdx.x; i < kLsQueries * W; i += blockDim.x) {
-        const int qi = i / W, w = i % W;
-        s_q[qi][w] = (static_cast<uint32_t>(qi) < nql) ? a.queries[static_cast<uint64_t>(q0 + qi) * W + w] : 0ull;
+    for (int i = threadIdx.x; i < kLsQueries * NW; i += blockDim.x) {
+        const int qi = i / NW, w = i % NW;
+        uint32_t v = 0;
+        if (static_cast<uint32_t>(qi) < nql) {
+            const uint64_t word = a.queries[static_cast<uint64_t>(q0 + qi) * W + w / 2];
+            v = static_cast<uint32_t>(w & 1 ? word >> 32 : word);
+        }
+        s_q[qi][w] = v;
     }
     for (int i = threadIdx.x; i < kLsQueries; i += blockDim.x)
         s_thr[i] = (static_cast<uint32_t>(i) < nql) ? a.thr[q0 + i] : -1;
@@ -105,39 +117,41 @@ __global__ void __launch_bounds__(kLsThreads) linscan_kernel(ScanArgs a) {
     const uint64_t begin = static_cast<uint64_t>(blockIdx.y) * a.split_len;
     const uint64_t end = min(a.n, begin + a.split_len);
     int tile_no = 0;
-    for (uint64_t t0 = begin; t0 < end; t0 += kLsTile, ++tile_no) {
-        uint64_t c[kLsCodesPerThread][W];
-        uint64_t idx[kLsCodesPerThread];
+    for (uint64_t t0 = begin; t0 < end; t0 += kTile, ++tile_no) {
+        const bool full = t0 + kTile <= end;   // only the last tile checks its codes
+        uint32_t c[J][NW];
+        bool ok[J];
 #pragma unroll
-        for (int jj = 0; jj < kLsCodesPerThread; ++jj) {
-            idx[jj] = t0 + static_cast<uint64_t>(jj) * kLsThreads + threadIdx.x;
-            const Code<W> v = (idx[jj] < end) ? load_code<W>(a.codes, idx[jj]) : Code<W>{};
+        for (int jj = 0; jj < J; ++jj) {
+            const uint64_t i = t0 + static_cast<uint64_t>(jj) * kLsThreads + threadIdx.x;
+            ok[jj] = full || i < end;
+            const Code<W> v = ok[jj] ? load_code<W>(a.codes, i) : Code<W>{};
 #pragma unroll
-            for (int w = 0; w < W; ++w) c[jj][w] = v.w[w];
+            for (int w = 0; w < W; ++w) {
+                c[jj][2 * w] = static_cast<uint32_t>(v.w[w]);
+                c[jj][2 * w + 1] = static_cast<uint32_t>(v.w[w] >> 32);
+            }
         }
         for (uint32_t qi = 0; qi < nql; ++qi) {
-            uint64_t g[W];
+            uint32_t g[NW];
 #pragma unroll
-            for (int w = 0; w < W; ++w) g[w] = s_q[qi][w];
+            for (int w = 0; w < NW; ++w) g[w] = s_q[qi][w];
             const int th = s_thr[qi];
 #pragma unroll
-            for (int jj = 0; jj < kLsCodesPerThread; ++jj) {
-                uint64_t x[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) x[w] = c[jj][w] ^ g[w];
-                const int lb = or_bound<W, G>(x);
-                if (lb <= th && idx[jj] < end) {
-                    int d = lb;
-                    if constexpr (G != 1) d = or_bound<W, 1>(x);
+            for (int jj = 0; jj < J; ++jj) {
+                const int lb = or_bound32<NW, G>(c[jj], g);
+                if (lb <= th && (full || ok[jj])) {
+                    const int d = (G == 1) ? lb : or_bound32<NW, 1>(c[jj], g);
                     if (d <= th) {
                         const uint32_t q = q0 + qi;
+                        const uint32_t id = static_cast<uint32_t>(t0 + static_cast<uint64_t>(jj) * kLsThreads + threadIdx.x);
                         const uint32_t p = atomicAdd(&a.cnt[q], 1u);
                         if (!a.second_pass) {
-                            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, static_cast<uint32_t>(idx[jj]));
+                            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, id);
                             atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.qbits + 1) + d], 1u);
                         } else {
                             const uint64_t slot = a.base[q] + p;
-                            if (slot < a.base[q + 1]) a.buf[slot] = pack_entry(d, static_cast<uint32_t>(idx[jj]));
+                            if (slot < a.base[q + 1]) a.buf[slot] = pack_entry(d, id);
                             else atomicExch(a.err, 1);
                         }
                     }
@@ -267,6 +281,8 @@ mih_status launch_scan_w(const ScanArgs& a, int G, dim3 grid, cudaStream_t s) {
     if (G >= 2) return launch_scan_wg<W, 2>(a, grid, s);
     return launch_scan_wg<W, 1>(a, grid, s);
 }
+// (split lengths are multiples of kLsTile = 2048 codes, a multiple of every
+// per-W tile, so only each CTA's last tile can be partial)
 
 mih_status launch_scan(const ScanArgs& a, int W, int G, dim3 grid, cudaStream_t s) {
     if (W == 1) return launch_scan_w<1>(a, G, grid, s);
@@ -349,7 +365,11 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         MIH_CUDA(cudaMemcpyAsync(hthr.data(), thr, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, s));
         MIH_CUDA(cudaStreamSynchronize(s));
         std::nth_element(hthr.begin(), hthr.begin() + nq / 2, hthr.end());
+#ifdef MIH_LINSCAN_G
+        const int G = MIH_LINSCAN_G;   // build-time override for tuning
+#else
         const int G = choose_group(W, hthr[nq / 2]);
+#endif
 
         const uint32_t qtiles = (nq + kLsQueries - 1) / kLsQueries;
         // enough CTA columns to fill the GPU about 4 times over

@@ -552,7 +552,10 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
 // mbarrier) of the next stage while the warp verifies the current one.  Every
 // wait on an mbarrier is bounded; on expiry the kernel raises a.timeout,
 // waits (bounded) for its own copies still in flight and leaves.
-constexpr uint32_t kStageBytes = 4096;
+#ifndef MIH_STAGE_BYTES
+#define MIH_STAGE_BYTES 4096
+#endif
+constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;
 constexpr int kStreamWarps = 8;
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kStageSlot = kStageBytes + 16;   // + one 8-byte code of realignment (W = 1)
