@@ -382,7 +382,10 @@ def run_ours(a):
         if main_ms > 0 else None
     ratio = traffic_ratio() if (q == 128 and kind == "lsh") else None
     traffic = ratio * alg_bytes / max(main_launches, 1) if ratio else None
-    roofline = {"bound": "hbm", "kernel": "search_kernel+search_big_kernel (fused MIH search)",
+    # main_ms is the span of the wave-loop graph: the fused search kernels plus
+    # each wave's planning and stopping-test kernels (a few % of it), so the
+    # achieved rate is a slight underestimate for the search kernels alone
+    roofline = {"bound": "hbm", "kernel": "search_kernel+search_stream_kernel (fused MIH search, wave-loop graph span)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
                 "traffic_source": ("profiles/search_kernels_5e7x128_traffic.txt: dram bytes per algorithmic byte "

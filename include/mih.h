@@ -82,8 +82,22 @@ typedef struct {
                               of each query's own bucket in every table to get a
                               first bound on its k-th distance (results
                               unchanged).  0 = default (1024), negative = off. */
-    int32_t reserved[12];  /* must be zero */
+    int32_t executor;      /* How mih_knn runs its waves of Alg. 3 steps (results
+                              unchanged): MIH_EXEC_GRAPH = one CUDA graph whose
+                              while-loop node repeats the wave and its stopping
+                              test on the device, with no host round trip between
+                              waves; MIH_EXEC_HOST = a host loop that reads the
+                              number of active queries after every wave.
+                              0 = MIH_EXEC_AUTO (the graph). */
+    int32_t reserved[11];  /* must be zero */
 } mih_params;
+
+/* mih_params.executor (not part of the paper: a launch strategy). */
+enum {
+    MIH_EXEC_AUTO = 0,
+    MIH_EXEC_HOST = 1,
+    MIH_EXEC_GRAPH = 2
+};
 
 /* Aggregate work counters of one mih_knn / mih_rnear call (host struct). */
 typedef struct {

@@ -22,6 +22,7 @@ _lib = None
 
 MIH_OK, MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EOVERFLOW, MIH_ETIMEOUT, MIH_EINTERNAL = range(7)
 MIH_TABLE_AUTO, MIH_TABLE_DIRECT, MIH_TABLE_SPARSE = 0, 1, 2
+MIH_EXEC_AUTO, MIH_EXEC_HOST, MIH_EXEC_GRAPH = 0, 1, 2
 MIH_MAX_K = 8192
 PAD_ID = 0xFFFFFFFF
 
@@ -41,7 +42,8 @@ class MihError(RuntimeError):
 
 class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
-                ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("reserved", ctypes.c_int32 * 12)]
+                ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("executor", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 11)]
 
 
 class mih_stats(ctypes.Structure):
@@ -227,13 +229,14 @@ class MihIndex:
 
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
-              inline_codes: int = 0, probe: int = 0, stream=None) -> MihIndex:
+              inline_codes: int = 0, probe: int = 0, executor: int = MIH_EXEC_AUTO, stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
     p.scan_factor = scan_factor
     p.inline_codes = inline_codes
     p.probe = probe
+    p.executor = executor
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)

@@ -52,6 +52,11 @@ cudaEvent_t next_event() {
 }  // namespace
 
 void note_launch() { g_prof.cur.launches++; }
+uint64_t launches_so_far() { return g_prof.cur.launches; }
+void add_launches(uint64_t launches, uint64_t main_launches) {
+    g_prof.cur.launches += launches;
+    g_prof.cur.main_launches += main_launches;
+}
 
 void main_kernel_begin(cudaStream_t s) {
     g_prof.cur.main_launches++;

@@ -304,11 +304,15 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     }
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
-        for (int i = 0; i < 12; ++i)
+        for (int i = 0; i < 11; ++i)
             if (params->reserved[i] != 0) {
                 set_error("mih_build: params.reserved must be zero");
                 return MIH_EINVAL;
             }
+        if (params->executor < MIH_EXEC_AUTO || params->executor > MIH_EXEC_GRAPH) {
+            set_error("mih_build: unknown executor %d", params->executor);
+            return MIH_EINVAL;
+        }
         kind_req = params->table_kind;
         if (kind_req < MIH_TABLE_AUTO || kind_req > MIH_TABLE_SPARSE) {
             set_error("mih_build: unknown table_kind %d", kind_req);
@@ -336,6 +340,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->codes = codes;
     ix->scan_factor = params ? params->scan_factor : 0;
     ix->probe = (!params || params->probe == 0) ? 1024 : (params->probe < 0 ? 0 : params->probe);
+    ix->executor = params ? params->executor : MIH_EXEC_AUTO;
     {
         // Inline codes: m * n * q/8 bytes on top of ids (4 m n) and tables;
         // automatic when the whole index fits in half the free memory.

@@ -22,4 +22,5 @@ struct mih_index {
     int scan_factor = 0;                        // lookup budget factor (see mih_params)
     bool inline_codes = false;                  // tables hold codes in bucket order
     int probe = 1024;                           // bound-probe entries per bucket (0 = off)
+    int executor = 0;                           // MIH_EXEC_* for the k-NN wave loop
 };

@@ -19,6 +19,8 @@ void clear_error();
 // Per-call profile (mih_last_profile): launch counts and, with timing on,
 // CUDA-event times of the main kernels.  A CallScope brackets one C-ABI call.
 void note_launch();
+uint64_t launches_so_far();                                  // launches counted in this call
+void add_launches(uint64_t launches, uint64_t main_launches);  // work a graph repeated on the device
 void main_kernel_begin(cudaStream_t s);
 void main_kernel_end(cudaStream_t s);
 class CallScope {
@@ -104,6 +106,8 @@ mih_status device_info(DeviceInfo* out);
 // Exclusive prefix sum over n elements; out may alias in.  Uses `ws`.
 mih_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, size_t n, Workspace& ws);
 mih_status scan_exclusive_u64(const uint64_t* in, uint64_t* out, size_t n, Workspace& ws);
+size_t scan_temp_u64(size_t n);
+mih_status scan_exclusive_u64_pre(const uint64_t* in, uint64_t* out, size_t n, uint64_t* tmp, cudaStream_t s);
 
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits
 // [0, bits), ping-ponging between the buffers and their alternates.  With

@@ -819,6 +819,17 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
     }
 }
 
+// Loop control of the graph executor, after the stopping test of a wave:
+// counts the wave and lets the while node run its body again while a query is
+// still active, no bounded wait has expired and fewer than max_waves waves ran.
+__global__ void loop_control_kernel(cudaGraphConditionalHandle h, const unsigned int* __restrict__ active,
+                                    const int* __restrict__ timeout, unsigned int* __restrict__ waves,
+                                    unsigned int max_waves) {
+    const unsigned int w = *waves + 1;
+    *waves = w;
+    cudaGraphSetConditional(h, (*active != 0u && *timeout == 0 && w < max_waves) ? 1u : 0u);
+}
+
 // ------------------------------------------------------------ selection
 struct SelectArgs {
     uint32_t nq;
@@ -1095,51 +1106,63 @@ unsigned grid1(uint64_t n) {
     return static_cast<unsigned>(g ? g : 1);
 }
 
-// Persistent grids: as many CTAs as fit on the GPU at once.
+// Persistent grids: as many CTAs as fit on the GPU at once.  The occupancy
+// queries and the shared-memory attribute run once per kernel, before any
+// launch (and so never while a stream is being captured).
+struct GridCfg {
+    int bps = 0, bps_big = 0, bps_stream = 0;
+};
+
 template <int W, int MODE, bool ALIGNED>
-mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s) {
-    static int bps = 0, bps_big = 0;  // resident blocks per SM (same on every GB300)
-    if (bps == 0) {
-        int v = 0, w = 0;
+mih_status search_cfg(const GridCfg** out) {
+    static GridCfg cfg;
+    if (cfg.bps == 0) {
+        int v = 0, w = 0, x = 0;
+        const size_t smem = stream_smem_bytes();
         MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE, ALIGNED>, kSearchThreads, 0));
         MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, search_big_kernel<W, MODE, ALIGNED>, kSearchThreads,
                                                                0));
-        bps_big = w > 0 ? w : 1;
-        bps = v > 0 ? v : 1;
+        MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, search_stream_kernel<W, MODE, ALIGNED>,
+                                                               kStreamWarps * 32, smem));
+        cfg.bps_big = w > 0 ? w : 1;
+        cfg.bps_stream = x > 0 ? x : 1;
+        cfg.bps = v > 0 ? v : 1;
     }
-    search_kernel<W, MODE, ALIGNED><<<dev.sms * bps, kSearchThreads, 0, s>>>(a);
+    *out = &cfg;
+    return MIH_OK;
+}
+
+template <int W, int MODE, bool ALIGNED>
+mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch) {
+    const GridCfg* cfg = nullptr;
+    MIH_TRY((search_cfg<W, MODE, ALIGNED>(&cfg)));
+    if (!launch) return MIH_OK;
+    search_kernel<W, MODE, ALIGNED><<<dev.sms * cfg->bps, kSearchThreads, 0, s>>>(a);
     MIH_LAUNCH_CHECK();
     if (a.inline_codes) {
-        static int bps_stream = 0;
-        const size_t smem = stream_smem_bytes();
-        if (bps_stream == 0) {
-            MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-            int v = 0;
-            MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_stream_kernel<W, MODE, ALIGNED>,
-                                                                   kStreamWarps * 32, smem));
-            bps_stream = v > 0 ? v : 1;
-        }
-        search_stream_kernel<W, MODE, ALIGNED><<<dev.sms * bps_stream, kStreamWarps * 32, smem, s>>>(a);
+        search_stream_kernel<W, MODE, ALIGNED>
+            <<<dev.sms * cfg->bps_stream, kStreamWarps * 32, stream_smem_bytes(), s>>>(a);
     } else {
-        search_big_kernel<W, MODE, ALIGNED><<<dev.sms * bps_big, kSearchThreads, 0, s>>>(a);
+        search_big_kernel<W, MODE, ALIGNED><<<dev.sms * cfg->bps_big, kSearchThreads, 0, s>>>(a);
     }
     MIH_LAUNCH_CHECK();
     return MIH_OK;
 }
 
 template <int W, int MODE>
-mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s) {
+mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch) {
     // every substring is one whole 32-bit word exactly when m = 2W
-    if (a.m == 2 * W) return launch_search_wa<W, MODE, true>(a, dev, s);
-    return launch_search_wa<W, MODE, false>(a, dev, s);
+    if (a.m == 2 * W) return launch_search_wa<W, MODE, true>(a, dev, s, launch);
+    return launch_search_wa<W, MODE, false>(a, dev, s, launch);
 }
 
 template <int MODE>
-mih_status launch_search(const SearchArgs& a, int W, const DeviceInfo& dev, cudaStream_t s) {
-    if (W == 1) return launch_search_w<1, MODE>(a, dev, s);
-    if (W == 2) return launch_search_w<2, MODE>(a, dev, s);
-    return launch_search_w<4, MODE>(a, dev, s);
+mih_status launch_search(const SearchArgs& a, int W, const DeviceInfo& dev, cudaStream_t s, bool launch = true) {
+    if (W == 1) return launch_search_w<1, MODE>(a, dev, s, launch);
+    if (W == 2) return launch_search_w<2, MODE>(a, dev, s, launch);
+    return launch_search_w<4, MODE>(a, dev, s, launch);
 }
 
 // Per-launch work state (chunk offsets, counters, big list).
@@ -1149,6 +1172,7 @@ struct Plan {
     BigSlice* big = nullptr;
     uint32_t big_cap = 0;
     int* timeout = nullptr;                  // raised by a bounded wait that gave up
+    uint64_t* scan_tmp = nullptr;            // block sums of the chunk-offset scan (graph mode)
 };
 
 mih_status plan_alloc(Plan& p, uint32_t nq, Workspace& ws) {
@@ -1174,14 +1198,19 @@ mih_status check_timeout(const Plan& p, cudaStream_t s) {
 }
 
 // Compute chunk offsets for the current step ranges and run one search launch.
+// With a capture stream cs the launches are recorded into a graph body on cs
+// (nothing is allocated and no event is recorded); else they run on the
+// workspace's stream.
 template <int MODE>
 mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
-                    const DeviceInfo& dev, Workspace& ws) {
-    cudaStream_t s = ws.stream();
+                    const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr) {
+    const bool in_graph = cs != nullptr;
+    cudaStream_t s = in_graph ? cs : ws.stream();
     plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
                                                       p.chunk_off);
     MIH_LAUNCH_CHECK();
-    MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
+    if (in_graph) MIH_TRY(scan_exclusive_u64_pre(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, p.scan_tmp, s));
+    else MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
     MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
     a.t_lo = t_lo;
     a.t_hi = t_hi;
@@ -1193,6 +1222,7 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
     a.big_next = a.big_count + 1;
     a.inline_codes = ix->inline_codes ? 1 : 0;
     a.timeout = p.timeout;
+    if (in_graph) return launch_search<MODE>(a, ix->W, dev, s);   // events cannot sit in a loop body
     main_kernel_begin(s);
     const mih_status st = launch_search<MODE>(a, ix->W, dev, s);
     main_kernel_end(s);
@@ -1212,6 +1242,70 @@ unsigned long long host_binom(int n, int k) {
     unsigned long long c = 1;
     for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
     return c;
+}
+
+// A non-blocking stream per device and host thread on which graph bodies are
+// captured (capture cannot run on the legacy default stream a caller may use).
+mih_status capture_stream(cudaStream_t* out) {
+    constexpr int kDevs = 64;
+    static thread_local cudaStream_t cs[kDevs] = {};
+    int d = 0;
+    MIH_CUDA(cudaGetDevice(&d));
+    if (d < 0 || d >= kDevs) {
+        set_error("device ordinal %d out of range", d);
+        return MIH_EINVAL;
+    }
+    if (!cs[d]) MIH_CUDA(cudaStreamCreateWithFlags(&cs[d], cudaStreamNonBlocking));
+    *out = cs[d];
+    return MIH_OK;
+}
+
+struct GraphGuard {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    ~GraphGuard() {
+        if (e) cudaGraphExecDestroy(e);
+        if (g) cudaGraphDestroy(g);
+    }
+};
+
+// Runs body(cs) -- launches recorded on the capture stream cs -- as the body of
+// a while-loop graph node on stream s, the first iteration unconditionally.
+// The body must end with loop_control_kernel on `h`.  Returns the launches
+// recorded in one body; the graph launch counts as one main launch.  The
+// caller synchronises before destroying `gg`.
+template <class Body>
+mih_status launch_while_graph(GraphGuard& gg, cudaStream_t s, uint64_t* body_launches, Body&& body) {
+    cudaStream_t cs = nullptr;
+    MIH_TRY(capture_stream(&cs));
+    MIH_CUDA(cudaGraphCreate(&gg.g, 0));
+    cudaGraphConditionalHandle h;
+    MIH_CUDA(cudaGraphConditionalHandleCreate(&h, gg.g, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    MIH_CUDA(cudaGraphAddNode(&node, gg.g, nullptr, nullptr, 0, &np));
+    cudaGraph_t loop_body = np.conditional.phGraph_out[0];
+    const uint64_t l0 = launches_so_far();
+    MIH_CUDA(cudaStreamBeginCaptureToGraph(cs, loop_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const mih_status st = body(cs, h);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &captured);
+    if (st != MIH_OK) {
+        cudaGetLastError();
+        return st;
+    }
+    MIH_CUDA(ce);
+    *body_launches = launches_so_far() - l0;
+    MIH_CUDA(cudaGraphInstantiate(&gg.e, gg.g, 0));
+    main_kernel_begin(s);  // the span covers every wave (with its planning and stopping test)
+    const cudaError_t le = cudaGraphLaunch(gg.e, s);
+    main_kernel_end(s);
+    MIH_CUDA(le);
+    return MIH_OK;
 }
 
 mih_status check_flag(const int* err, const char* what, cudaStream_t s) {
@@ -1461,24 +1555,59 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     a.n = ix->n;
     a.exact_stats = query_stats != nullptr ? 1 : 0;
 
+    // One wave: every active query runs its current Alg. 3 step(s), then the
+    // stopping test advances or retires it.  cs = capture stream (graph) or 0.
+    auto wave = [&](cudaStream_t cs) -> mih_status {
+        cudaStream_t ws_s = cs ? cs : s;
+        MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs));
+        MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), ws_s));
+        knn_stop_kernel<<<grid1(nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
+                                                    hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
+                                                    exh, budget);
+        MIH_LAUNCH_CHECK();
+        return MIH_OK;
+    };
+    // At most q + 1 waves: step t <= q reaches every code (Prop. 1 with r = q).
+    const unsigned int max_waves = static_cast<unsigned int>(qb) + 1;
     uint64_t waves = 0;
-    if (ix->n > 0) {
-        for (int t = 0; t <= qb; ++t) {
-            MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws));
+    if (ix->n > 0 && ix->executor == MIH_EXEC_HOST) {
+        for (unsigned int w = 0; w < max_waves; ++w) {
+            MIH_TRY(wave(nullptr));
             ++waves;
-            MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), s));
-            knn_stop_kernel<<<grid1(nq), 256, 0, s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
-                                                     hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
-                                                     exh, budget);
-            MIH_LAUNCH_CHECK();
             unsigned int hact = 0;
             MIH_CUDA(cudaMemcpyAsync(&hact, active, sizeof(hact), cudaMemcpyDeviceToHost, s));
             MIH_TRY(check_timeout(plan, s));
             if (hact == 0) break;
-            if (t == qb) {
+            if (w + 1 == max_waves) {
                 set_error("mih_knn: queries still active after q steps");
                 return MIH_EINTERNAL;
             }
+        }
+    } else if (ix->n > 0) {
+        // The whole loop as one graph launch: a while node repeats the wave
+        // and the loop control on the device, with no host round trip.
+        unsigned int* wave_count;
+        MIH_TRY(ws.alloc(&wave_count, 1));
+        MIH_CUDA(cudaMemsetAsync(wave_count, 0, sizeof(unsigned int), s));
+        MIH_TRY(ws.alloc(&plan.scan_tmp, scan_temp_u64(static_cast<size_t>(nq) + 1)));
+        MIH_TRY(launch_search<kModeKnn>(a, ix->W, dev, s, false));   // kernel attributes, before capture
+        GraphGuard gg;
+        uint64_t body_launches = 0;
+        MIH_TRY(launch_while_graph(gg, s, &body_launches, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+            MIH_TRY(wave(cs));
+            loop_control_kernel<<<1, 1, 0, cs>>>(h, active, plan.timeout, wave_count, max_waves);
+            MIH_LAUNCH_CHECK();
+            return MIH_OK;
+        }));
+        unsigned int hw = 0, hact = 0;
+        MIH_CUDA(cudaMemcpyAsync(&hw, wave_count, sizeof(hw), cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaMemcpyAsync(&hact, active, sizeof(hact), cudaMemcpyDeviceToHost, s));
+        MIH_TRY(check_timeout(plan, s));
+        waves = hw;
+        if (hw > 1) add_launches((hw - 1) * body_launches, hw - 1);
+        if (hact != 0) {
+            set_error("mih_knn: queries still active after q steps");
+            return MIH_EINTERNAL;
         }
     }
 

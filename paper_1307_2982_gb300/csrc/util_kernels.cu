@@ -227,6 +227,32 @@ mih_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, size_t n, Works
     return scan_exclusive<uint32_t>(in, out, n, ws);
 }
 
+// Scan with caller-provided block sums (no allocation; usable while a stream
+// is being captured into a graph): tmp must hold scan_temp_u64(n) elements.
+size_t scan_temp_u64(size_t n) {
+    size_t total = 0;
+    while (n > static_cast<size_t>(kScanTile)) {
+        n = (n + kScanTile - 1) / kScanTile;
+        total += n;
+    }
+    return total > 0 ? total : 1;
+}
+
+mih_status scan_exclusive_u64_pre(const uint64_t* in, uint64_t* out, size_t n, uint64_t* tmp, cudaStream_t s) {
+    if (n == 0) return MIH_OK;
+    const size_t blocks = (n + kScanTile - 1) / kScanTile;
+    uint64_t* sums = nullptr;
+    if (blocks > 1) {
+        sums = tmp;
+        scan_reduce_kernel<uint64_t><<<static_cast<unsigned>(blocks), kScanThreads, 0, s>>>(in, n, sums);
+        MIH_LAUNCH_CHECK();
+        MIH_TRY(scan_exclusive_u64_pre(sums, sums, blocks, tmp + blocks, s));
+    }
+    scan_down_kernel<uint64_t><<<static_cast<unsigned>(blocks), kScanThreads, 0, s>>>(in, out, n, sums);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
 mih_status scan_exclusive_u64(const uint64_t* in, uint64_t* out, size_t n, Workspace& ws) {
     return scan_exclusive<uint64_t>(in, out, n, ws);
 }

@@ -112,6 +112,30 @@ def test_mih_work_counters_match_alg3(gpu_lib, orc, kind, q, m, n):
             assert tuple(st[i]) == tuple(cnt), (i, k, st[i], cnt)
 
 
+@pytest.mark.parametrize("kind,q,m,n", [("lsh", 128, 6, 200_003), ("uniform", 64, 3, 50_000),
+                                        ("lsh", 256, 9, 60_001)])
+def test_graph_and_host_executors_agree(gpu_lib, orc, kind, q, m, n):
+    """The wave loop as one CUDA graph (while node) and as a host loop give the
+    oracle's results and the same work counters, wave for wave."""
+    mih = gpu_lib
+    db, qs = workload(kind, q, n, 257, seed=21)
+    codes, queries = to_dev(db), to_dev(qs)
+    ixg = mih.mih_build(codes, q, m, executor=mih.MIH_EXEC_GRAPH)
+    ixh = mih.mih_build(codes, q, m, executor=mih.MIH_EXEC_HOST)
+    for k in (1, 100):
+        want_ids, want_dist = orc.knn(db, qs, k)
+        for qstats in (False, True):
+            rg = mih.mih_knn(ixg, queries, k, query_stats=qstats)
+            rh = mih.mih_knn(ixh, queries, k, query_stats=qstats)
+            for r in (rg, rh):
+                assert np.array_equal(ids_of(r["ids"]), want_ids), (k, qstats)
+                assert np.array_equal(host(r["dist"]), want_dist), (k, qstats)
+            assert rg["stats"] == rh["stats"], (k, qstats, rg["stats"], rh["stats"])
+            assert rg["stats"]["waves"] >= 1
+            if qstats:
+                assert np.array_equal(host(rg["query_stats"]), host(rh["query_stats"]))
+
+
 def test_per_query_k_and_padding(gpu_lib, orc):
     mih = gpu_lib
     import torch
