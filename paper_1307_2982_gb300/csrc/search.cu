@@ -591,18 +591,48 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // One stage: entries [pos, pos + cnt) of a slice ending at `end`, all of
-// query q at step t.  Warp-uniform.
+// query q at step t, with the query's state for verifying them (loaded when
+// the slice's first stage is issued, two stages before it is verified).
+// Warp-uniform.
+template <int W>
 struct Stage {
     uint32_t q;
     int t;
     uint32_t pos, cnt, end;
     bool valid;
+    int bnd, hd;
+    Code<W> g;
 };
 
+// Slices are taken from the wave's list through a shared counter.  To keep
+// that round trip off the critical path each warp holds the index of its next
+// slice (fetched one slice ahead) and that slice's descriptor (loaded one
+// slice ahead): starting a slice uses only values already in registers.
+struct SliceFeed {
+    uint32_t next_idx;   // index of the slice after `ahead` (warp-uniform)
+    BigSlice ahead;      // descriptor of the next slice (q = kPadId past the end)
+};
+
+__device__ __forceinline__ BigSlice load_slice(const SearchArgs& a, uint32_t i, unsigned int count) {
+    BigSlice bs;
+    bs.q = kPadId;
+    bs.t = -1;
+    bs.begin = bs.end = 0;
+    if (i < count) bs = a.big[i];
+    return bs;
+}
+
+__device__ __forceinline__ uint32_t fetch_slice_index(const SearchArgs& a) {
+    uint32_t i = 0;
+    if (lane_id() == 0) i = atomicAdd(a.big_next, 1u);
+    return __shfl_sync(0xFFFFFFFFu, i, 0);
+}
+
 template <int W>
-__device__ __forceinline__ Stage next_stage(const SearchArgs& a, const Stage& st, unsigned int count) {
+__device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<W>& st, unsigned int count,
+                                               SliceFeed& feed) {
     constexpr uint32_t kPer = kStageBytes / (8 * W);
-    Stage r = st;
+    Stage<W> r = st;
     if (!st.valid) return r;
     if (st.pos + st.cnt < st.end) {
         r.pos = st.pos + st.cnt;
@@ -610,20 +640,24 @@ __device__ __forceinline__ Stage next_stage(const SearchArgs& a, const Stage& st
         return r;
     }
     for (;;) {
-        unsigned int i = 0;
-        if (lane_id() == 0) i = atomicAdd(a.big_next, 1u);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= count) {
+        const BigSlice bs = feed.ahead;
+        if (bs.t < 0) {   // the list is exhausted
             r.valid = false;
             return r;
         }
-        const BigSlice bs = a.big[i];
-        if (bs.q == kPadId) continue;
+        // refill the feed: descriptor of the index fetched a slice ago, and
+        // the index after it (both complete while this slice is verified)
+        feed.ahead = load_slice(a, feed.next_idx, count);
+        feed.next_idx = fetch_slice_index(a);
+        if (bs.q == kPadId) continue;   // reserved but never filled
         r.q = bs.q;
         r.t = bs.t;
         r.pos = bs.begin;
         r.end = bs.end;
         r.cnt = min(kPer, bs.end - bs.begin);
+        r.bnd = __ldg(a.bound + bs.q);
+        r.hd = a.hist_done ? __ldg(a.hist_done + bs.q) : -1;
+        r.g = load_query<W>(a.queries, bs.q);
         return r;
     }
 }
@@ -631,7 +665,7 @@ __device__ __forceinline__ Stage next_stage(const SearchArgs& a, const Stage& st
 // Lane 0 starts the copy of stage st into slot `buf`; returns the code offset
 // of the stage inside the slot (nonzero only when W = 1 realigns to 16 bytes).
 template <int W>
-__device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage& st, unsigned char* buf,
+__device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage<W>& st, unsigned char* buf,
                                                 uint64_t* bar) {
     const uint64_t* codes = a.tables[st.t % a.m].codes;
     uint32_t lo = st.pos, shift = 0, bytes = st.cnt * 8u * W;
@@ -648,7 +682,7 @@ __device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage
 }
 
 template <int W, int MODE, bool ALIGNED>
-__global__ void __launch_bounds__(kStreamWarps * 32) search_stream_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kStreamWarps * 32, 3) search_stream_kernel(SearchArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_len[kMaxTables];
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
@@ -666,40 +700,47 @@ __global__ void __launch_bounds__(kStreamWarps * 32) search_stream_kernel(Search
     __syncthreads();
     const Layout L{s_len, s_mask};
     uint32_t* whist = s_hist[warp];
-    unsigned char* slot[2] = {dsm + (2 * warp) * kStageSlot, dsm + (2 * warp + 1) * kStageSlot};
-    uint64_t* bar[2] = {&s_bar[warp][0], &s_bar[warp][1]};
-    uint32_t parity[2] = {0u, 0u};
-    uint32_t shift[2] = {0u, 0u};
+    // slot/barrier b of this warp (b = 0, 1), selected without indexing
+    // register arrays (which would put them in local memory)
+    unsigned char* const slot0 = dsm + (2 * warp) * kStageSlot;
+    uint64_t* const bar0 = &s_bar[warp][0];
+    uint32_t parities = 0u;   // bit b: phase parity of barrier b
+    uint32_t shift0 = 0u, shift1 = 0u;
     const unsigned int count = min(*a.big_count, a.big_cap);
 
-    Stage none;
+    SliceFeed feed;
+    feed.ahead = load_slice(a, fetch_slice_index(a), count);
+    feed.next_idx = fetch_slice_index(a);
+    Stage<W> none;
     none.valid = true;
     none.pos = none.cnt = none.end = 0;
     none.q = 0;
     none.t = 0;
-    Stage cur = next_stage<W>(a, none, count);
+    none.bnd = none.hd = 0;
+    Stage<W> cur = next_stage<W>(a, none, count, feed);
     if (!cur.valid) return;
-    shift[0] = issue_stage<W>(a, cur, slot[0], bar[0]);
-    Stage nxt = next_stage<W>(a, cur, count);
-    if (nxt.valid) shift[1] = issue_stage<W>(a, nxt, slot[1], bar[1]);
+    shift0 = issue_stage<W>(a, cur, slot0, bar0);
+    Stage<W> nxt = next_stage<W>(a, cur, count, feed);
+    if (nxt.valid) shift1 = issue_stage<W>(a, nxt, slot0 + kStageSlot, bar0 + 1);
+    // entries per lane and batch (a 4 KB stage is 1, 2 or 4 batches for W = 4, 2, 1)
+    constexpr int kPer = static_cast<int>(kStageBytes / (8 * W));
+    constexpr int B = kPer / 32 < 4 ? kPer / 32 : 4;
     int b = 0;
+    uint32_t unique = 0;
     while (cur.valid) {
-        if (!mbar_wait_bounded(bar[b], parity[b])) {
+        unsigned char* const slot_b = slot0 + b * kStageSlot;
+        uint64_t* const bar_b = bar0 + b;
+        if (!mbar_wait_bounded(bar_b, (parities >> b) & 1u)) {
             if (lane == 0) atomicExch(a.timeout, 1);
-            if (nxt.valid) mbar_wait_bounded(bar[b ^ 1], parity[b ^ 1]);   // let our other copy land
+            if (nxt.valid) mbar_wait_bounded(bar0 + (b ^ 1), (parities >> (b ^ 1)) & 1u);   // let our other copy land
             return;
         }
-        parity[b] ^= 1u;
+        parities ^= 1u << b;
         // verify the stage out of shared memory
         const int j = cur.t % a.m, rho = cur.t / a.m;
-        const Code<W> g = load_query<W>(a.queries, cur.q);
-        const TableDesc& tab = a.tables[j];
-        const CandSource src{tab.codes, tab.ids, false};
-        const int hd = a.hist_done ? __ldg(a.hist_done + cur.q) : -1;
-        const int bnd = __ldg(a.bound + cur.q);
-        const Code<W>* sc = reinterpret_cast<const Code<W>*>(slot[b]) + shift[b];
-        uint32_t unique = 0, unused = 0;
-        constexpr int B = 4;
+        const CandSource src{nullptr, a.tables[j].ids, false};
+        const Code<W>* sc = reinterpret_cast<const Code<W>*>(slot_b) + (b ? shift1 : shift0);
+        uint32_t unused = 0;
         for (uint32_t base = 0; base < cur.cnt; base += 32 * B) {
             uint32_t pos[B], id[B];
             bool valid[B];
@@ -715,17 +756,26 @@ __global__ void __launch_bounds__(kStreamWarps * 32) search_stream_kernel(Search
 #pragma unroll
                     for (int w = 0; w < W; ++w) c[k].w[w] = 0ull;
             }
-            process_loaded<W, MODE, ALIGNED, B>(a, L, whist, cur.q, j, rho, -1, hd, bnd, g, src, pos, valid, c, id,
-                                                unique, unused);
+            process_loaded<W, MODE, ALIGNED, B>(a, L, whist, cur.q, j, rho, -1, cur.hd, cur.bnd, cur.g, src, pos,
+                                                valid, c, id, unique, unused);
         }
-        if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(cur.q) * (a.q + 1), a.q);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
-        if (lane == 0 && a.qstats) atomicAdd(&a.qstats[4ull * cur.q + 2], static_cast<unsigned long long>(unique));
         __syncwarp();
         // the slot just read takes the stage after next
-        const Stage nn = next_stage<W>(a, nxt, count);
-        if (nn.valid) shift[b] = issue_stage<W>(a, nn, slot[b], bar[b]);
+        const Stage<W> nn = next_stage<W>(a, nxt, count, feed);
+        if (nn.valid) {
+            const uint32_t sh = issue_stage<W>(a, nn, slot_b, bar_b);
+            if (b) shift1 = sh; else shift0 = sh;
+        }
+        // histogram and counters go out once the warp leaves this query
+        if (!nxt.valid || nxt.q != cur.q) {
+            if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(cur.q) * (a.q + 1), a.q);
+            if (a.qstats) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) unique += __shfl_down_sync(0xFFFFFFFFu, unique, o);
+                if (lane == 0) atomicAdd(&a.qstats[4ull * cur.q + 2], static_cast<unsigned long long>(unique));
+            }
+            unique = 0;
+        }
         cur = nxt;
         nxt = nn;
         b ^= 1;
