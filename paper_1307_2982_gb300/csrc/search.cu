@@ -331,37 +331,55 @@ __device__ __forceinline__ void flush_hist(uint32_t* whist, uint32_t* ghist, int
     __syncwarp();
 }
 
-// Warp-cooperative pass over the union of up to 32 buckets [b, b + sz),
-// 32 * B candidates per round.
-template <int W, int MODE, bool ALIGNED, int B>
-__device__ __forceinline__ void scan_buckets(const SearchArgs& a, const Layout& L,
-                                             uint32_t* whist, const CandSource& src, uint32_t q, int j,
-                                             int rho, int hist_done, int bnd, const Code<W>& g, uint32_t b,
-                                             uint32_t sz, uint32_t& unique_acc) {
-    const uint32_t incl = warp_inclusive_scan(sz);
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    const uint32_t excl = incl - sz;
-    const uint32_t lane = lane_id();
-    for (uint32_t base = 0; base < total; base += 32 * B) {
-        uint32_t pos[B];
-        bool valid[B];
+// Buckets of R keys of one lane, with every table read of the R lookups in
+// flight together: the first slot group of each key's probe sequence, then
+// the bucket bounds.  A key whose first group neither holds it nor ends its
+// probe sequence (rare at the tables' load factor) takes the full lookup.
+template <int R>
+__device__ __forceinline__ void lookup_buckets(const TableDesc& t, const uint32_t (&key)[R], int mine,
+                                               uint32_t (&b)[R], uint32_t (&e)[R]) {
+    if (t.kind == MIH_TABLE_DIRECT) {
 #pragma unroll
-        for (int k = 0; k < B; ++k) {
-            const uint32_t idx = base + k * 32 + lane;
-            int owner = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, owner + step);
-                if (e <= idx) owner += step;
-            }
-            const uint32_t ob = __shfl_sync(0xFFFFFFFFu, b, owner);
-            const uint32_t oe = __shfl_sync(0xFFFFFFFFu, excl, owner);
-            valid[k] = idx < total;
-            pos[k] = valid[k] ? ob + (idx - oe) : 0u;
+        for (int r = 0; r < R; ++r) {
+            b[r] = r < mine ? __ldg(t.offsets + key[r]) : 0u;
+            e[r] = r < mine ? __ldg(t.offsets + key[r] + 1) : 0u;
         }
-        uint32_t unused = 0;
-        handle_batch<W, MODE, ALIGNED, B>(a, L, whist, q, j, rho, -1, hist_done, bnd, g, src, pos, valid,
-                                          unique_acc, unused);
+        return;
+    }
+    uint32_t rank[R];
+    bool open[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        uint4 s01 = make_uint4(0u, kEmptySlot, 0u, kEmptySlot);
+        uint4 s23 = s01;
+        if (r < mine) {
+            const uint4* s4 = reinterpret_cast<const uint4*>(t.slots + 4 * (hash_key(key[r]) & t.bucket_mask));
+            s01 = __ldg(s4);
+            s23 = __ldg(s4 + 1);
+        }
+        // first match or first empty slot of the group decides
+        uint32_t rk = kEmptySlot;
+        bool op = false;
+        if (s01.y == kEmptySlot) op = true;
+        else if (s01.x == key[r]) rk = s01.y;
+        else if (s01.w == kEmptySlot) op = true;
+        else if (s01.z == key[r]) rk = s01.w;
+        else if (s23.y == kEmptySlot) op = true;
+        else if (s23.x == key[r]) rk = s23.y;
+        else if (s23.w == kEmptySlot) op = true;
+        else if (s23.z == key[r]) rk = s23.w;
+        rank[r] = rk;
+        open[r] = op || r >= mine;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        b[r] = e[r] = 0u;
+        if (rank[r] != kEmptySlot) {
+            b[r] = __ldg(t.offsets + rank[r]);
+            e[r] = __ldg(t.offsets + rank[r] + 1);
+        } else if (!open[r]) {
+            lookup_bucket(t, key[r], b[r], e[r]);   // group full of other keys: keep probing
+        }
     }
 }
 
@@ -376,6 +394,7 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
     __shared__ int s_len[kMaxTables];
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
     __shared__ uint32_t s_hist[kWarps][kHistBins];
+    __shared__ uint2 s_list[kWarps][kChunkKeys];   // a chunk's nonempty buckets: {begin, first union index}
     for (int j = threadIdx.x; j < a.m; j += blockDim.x) s_off[j] = a.tables[j].off;
     build_layout(a.tables, a.m, W, s_len, s_mask);
     for (int i = threadIdx.x; i < kWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
@@ -448,14 +467,19 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
         const TableDesc& tab = a.tables[j];
         const CandSource src = tab.codes ? CandSource{tab.codes, tab.ids, false} : CandSource{a.codes, tab.ids, true};
         uint64_t x = mine > 0 ? unrank_subset(first, s, rho) : 0ull;
-        uint32_t raw = 0, unique = 0;
+        uint32_t key[kKeysPerLane], bb[kKeysPerLane], ee[kKeysPerLane];
+#pragma unroll
         for (int r = 0; r < kKeysPerLane; ++r) {
-            uint32_t b = 0, e = 0;
-            if (r < mine) {
-                lookup_bucket(tab, gkey ^ static_cast<uint32_t>(x), b, e);
-                if (rho > 0 && r + 1 < mine) x = next_subset(x);
-            }
-            uint32_t sz = e - b;
+            key[r] = gkey ^ static_cast<uint32_t>(x);
+            if (rho > 0 && r + 1 < mine) x = next_subset(x);
+        }
+        lookup_buckets<kKeysPerLane>(tab, key, mine, bb, ee);
+        uint32_t raw = 0, unique = 0;
+        int nz = 0;
+        uint32_t tot = 0;
+#pragma unroll
+        for (int r = 0; r < kKeysPerLane; ++r) {
+            uint32_t sz = ee[r] - bb[r];
             if (sz > kBigBucket) {
                 // Hand the bucket to the slice kernel; if the list is full the
                 // reserved slots are marked empty and the warp scans it here.
@@ -466,8 +490,8 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
                     BigSlice bs;
                     bs.q = fits ? q : kPadId;
                     bs.t = t;
-                    bs.begin = b + i * kSliceEntries;
-                    bs.end = min(e, bs.begin + kSliceEntries);
+                    bs.begin = bb[r] + i * kSliceEntries;
+                    bs.end = min(ee[r], bs.begin + kSliceEntries);
                     a.big[at + i] = bs;
                 }
                 if (fits) {
@@ -476,8 +500,47 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
                 }
             }
             raw += sz;
-            if (__any_sync(0xFFFFFFFFu, sz != 0))
-                scan_buckets<W, MODE, ALIGNED, kBatch>(a, L, whist, src, q, j, rho, hd, bnd, g, b, sz, unique);
+            ee[r] = sz;   // from here on: entries this warp scans itself
+            nz += sz != 0 ? 1 : 0;
+            tot += sz;
+        }
+        // The warp scans the union of its nonempty small buckets, 32 * kBatch
+        // entries per round: list them (begin, first union index) in shared
+        // memory, and map a union index to its bucket by binary search.
+        const uint32_t nz_incl = warp_inclusive_scan(static_cast<uint32_t>(nz));
+        const uint32_t tot_incl = warp_inclusive_scan(tot);
+        const uint32_t n_list = __shfl_sync(0xFFFFFFFFu, nz_incl, 31);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, tot_incl, 31);
+        if (total > 0) {
+            uint2* list = s_list[threadIdx.x >> 5];
+            uint32_t at = nz_incl - nz, run = tot_incl - tot;
+#pragma unroll
+            for (int r = 0; r < kKeysPerLane; ++r)
+                if (ee[r] != 0) {
+                    list[at++] = make_uint2(bb[r], run);
+                    run += ee[r];
+                }
+            __syncwarp();
+            for (uint32_t base = 0; base < total; base += 32 * kBatch) {
+                uint32_t pos[kBatch];
+                bool valid[kBatch];
+#pragma unroll
+                for (int k = 0; k < kBatch; ++k) {
+                    const uint32_t idx = base + k * 32 + lane;
+                    uint32_t lo = 0, hi = n_list;   // last entry whose first index <= idx
+                    while (hi - lo > 1) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (list[mid].y <= idx) lo = mid; else hi = mid;
+                    }
+                    const uint2 ent = list[lo];
+                    valid[k] = idx < total;
+                    pos[k] = valid[k] ? ent.x + (idx - ent.y) : 0u;
+                }
+                uint32_t unused = 0;
+                handle_batch<W, MODE, ALIGNED, kBatch>(a, L, whist, q, j, rho, -1, hd, bnd, g, src, pos, valid,
+                                                       unique, unused);
+            }
+            __syncwarp();
         }
         if (MODE == kModeKnn) flush_hist(whist, ghist, a.q);
         // per-query counters (lookups, raw candidates, unique candidates) of
@@ -831,17 +894,32 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
     __shared__ int s_len[kMaxTables];
     for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
     __syncthreads();
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    // one warp per query: lane l sums bins [l * per, (l + 1) * per)
+    const uint32_t lane = lane_id();
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    const int per = (qbits + 1 + 31) / 32;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
         const int t = t_hi[q];
-        if (t < t_lo[q]) continue;  // retired earlier
+        if (t < t_lo[q]) continue;  // retired earlier (warp-uniform)
         const uint32_t kk = kk_of(kq, k_uniform, q, n);
         const uint32_t* h = hist + static_cast<uint64_t>(q) * (qbits + 1);
-        uint64_t cum = 0;
-        int first_reach = -1;
-        for (int d = 0; d <= qbits; ++d) {
-            cum += h[d];
-            if (first_reach < 0 && cum >= kk) first_reach = d;
+        const int d0 = static_cast<int>(lane) * per;
+        uint32_t part = 0;
+        for (int i = 0; i < per; ++i)
+            if (d0 + i <= qbits) part += h[d0 + i];
+        const uint32_t incl = warp_inclusive_scan(part);   // codes at distances < (lane + 1) * per
+        // first distance at which the cumulative count reaches min(k, n)
+        int reach = -1;
+        if (incl >= kk && incl - part < kk) {
+            uint32_t cum = incl - part;
+            for (int i = 0; i < per && reach < 0; ++i) {
+                cum += h[d0 + i];
+                if (cum >= kk) reach = d0 + i;
+            }
         }
+        const uint32_t who = __ballot_sync(0xFFFFFFFFu, reach >= 0);
+        const int first_reach = who ? __shfl_sync(0xFFFFFFFFu, reach, __ffs(who) - 1) : -1;
+        if (lane != 0) continue;
         const bool full = exh[q] != 0;  // this launch verified every remaining code
         if (first_reach >= 0 && (first_reach <= t || full)) {
             dk[q] = first_reach;            // every code within t bits (or all codes) is known
@@ -1611,7 +1689,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         cudaStream_t ws_s = cs ? cs : s;
         MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs));
         MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), ws_s));
-        knn_stop_kernel<<<grid1(nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
+        knn_stop_kernel<<<grid1(32ull * nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
                                                     hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
                                                     exh, budget);
         MIH_LAUNCH_CHECK();
