@@ -34,6 +34,8 @@ if ROOT not in sys.path:
 
 METRIC = "exact 100-NN queries/s on 1B×128-bit codes, MIH vs linear scan on GB300; p99 ms"
 
+# mih_params.executor values (include/mih.h)
+EXECUTORS = {"graph": 2, "host": 1}
 # candidate m for the autotuner (substrings of at most 32 bits)
 AUTOTUNE_M = {"H": [4, 5], "1": [3, 4, 5], "2": [5, 6, 7], "3": [2, 3, 4], "4": [8, 9, 10]}
 # workload name -> (kind, n, q, nq, k, m); "kper" = per-query log-uniform k
@@ -73,6 +75,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="use the workload's default m")
     ap.add_argument("--serve-qps", type=float, default=200_000.0, help="offered load of the serving check")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--executor", default="graph", choices=["graph", "host"],
+                    help="k-NN wave loop: one CUDA graph (while node) or a host loop (per-kernel profiling)")
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -304,7 +308,8 @@ def run_ours(a):
         hold = make_codes(kind, 1000, q, 5, dev)
         kk_tune = k if k != "kper" else 100
         t0 = time.perf_counter()
-        m, tune_ms = mih.mih_autotune(codes, q, hold, kk_tune, candidates=AUTOTUNE_M[a.workload], probe=a.probe)
+        m, tune_ms = mih.mih_autotune(codes, q, hold, kk_tune, candidates=AUTOTUNE_M[a.workload], probe=a.probe,
+                                      executor=EXECUTORS[a.executor])
         tune = {"candidates": AUTOTUNE_M[a.workload], "ms_per_query": {str(kq): v for kq, v in tune_ms.items()},
                 "chosen_m": m, "holdout_queries": 1000, "k": kk_tune, "seconds": time.perf_counter() - t0}
         del hold
@@ -313,7 +318,7 @@ def run_ours(a):
     # index build (Algorithm 1), timed on the device
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    index = mih.mih_build(codes, q, m, probe=a.probe)
+    index = mih.mih_build(codes, q, m, probe=a.probe, executor=EXECUTORS[a.executor])
     ev1.record()
     torch.cuda.synchronize()
     build_ms = ev0.elapsed_time(ev1)
@@ -488,7 +493,7 @@ def run_ours(a):
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (codes + tables, no flush)",
                    "substring_bits": info["substring_length"], "table_kind": info["table_kind"],
                    "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s,
-                   "inline_codes": info["inline_codes"], "autotune": tune},
+                   "inline_codes": info["inline_codes"], "executor": a.executor, "autotune": tune},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "mih_stats_per_step": {kk: v / a.steps for kk, v in stats_acc.items()},
         "linscan": linscan, "parity": parity, "serving": serve,
@@ -517,7 +522,7 @@ def run_serving(a):
         codes = make_codes(kind, n, q, 0, dev)
         torch.cuda.empty_cache()
         m = mih.mih_suggest_m(q, n)
-        idx.append(mih.mih_build(codes, q, m, probe=a.probe))
+        idx.append(mih.mih_build(codes, q, m, probe=a.probe, executor=EXECUTORS[a.executor]))
         dbs.append({"codes": kind, "n": n, "q": q, "m": m, "index_bytes": idx[-1].info()["index_bytes"]})
 
     def gen(d, c, sd):

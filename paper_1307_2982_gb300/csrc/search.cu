@@ -270,50 +270,59 @@ __device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout
     const int far = (bnd < 0 || a.exact_stats) ? 0x7FFFFFFF : bnd;
     const uint32_t lane = lane_id();
     const uint32_t lt = (1u << lane) - 1u;
+    // Distances and tests of all B candidates first; the kept entries of the
+    // batch then take one slot reservation (a single atomic) for the warp.
+    int dist[B];
+    uint32_t take_mask = 0;   // bit b: candidate b is stored / collected
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         int d = 0;
         bool keep = false, count = false;
         if (valid[b]) eval_candidate<W, ALIGNED>(a.m, L, j, rho, t_done, hist_done, far, g, c[b], d, keep, count);
+        dist[b] = d;
         if (j < 0) raw_acc += (valid[b] && count) ? 1u : 0u;
         if constexpr (MODE == kModeKnn) {
             if (keep && count) {
                 atomicAdd(&whist[d], 1u);
                 ++unique_acc;
             }
-            const bool store = keep && d <= bnd;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, store);
-            if (bal) {
-                uint32_t base = 0;
-                const int leader = __ffs(bal) - 1;
-                if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
-                base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                if (store) {
-                    const uint32_t p = base + __popc(bal & lt);
-                    const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
-                    if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, cid);
-                }
-            }
         } else {
-            const bool take = keep && d <= bnd;
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, take);
-            if (bal) {
-                const int leader = __ffs(bal) - 1;
-                uint32_t base = 0;
-                if (static_cast<int>(lane) == leader) base = atomicAdd(&a.cnt[q], static_cast<uint32_t>(__popc(bal)));
-                if constexpr (MODE == kModeCollect) {
-                    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                    if (take) {
-                        const uint64_t p = __ldg(a.out_base + q) + base + __popc(bal & lt);
-                        const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
-                        if (p < __ldg(a.out_base + q + 1))
-                            a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(d, cid);
-                        else
-                            atomicExch(a.err, 1);
-                    }
-                }
-            }
             unique_acc += keep ? 1u : 0u;
+        }
+        if (keep && d <= bnd) take_mask |= 1u << b;
+    }
+    if constexpr (MODE == kModeCount) {
+        const uint32_t mine = __popc(take_mask);
+        const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, mine);
+        if (total != 0 && lane == 0) atomicAdd(&a.cnt[q], total);
+        return;
+    }
+    if (!__any_sync(0xFFFFFFFFu, take_mask != 0)) return;
+    // lane offsets within the batch: candidates ordered by (b, lane)
+    uint32_t before[B];
+    uint32_t total = 0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (take_mask >> b) & 1u);
+        before[b] = total + __popc(bal & lt);
+        total += __popc(bal);
+    }
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&a.cnt[q], total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        if (!((take_mask >> b) & 1u)) continue;
+        const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
+        if constexpr (MODE == kModeKnn) {
+            const uint32_t p = base + before[b];
+            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(dist[b], cid);
+        } else {
+            const uint64_t p = __ldg(a.out_base + q) + base + before[b];
+            if (p < __ldg(a.out_base + q + 1))
+                a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(dist[b], cid);
+            else
+                atomicExch(a.err, 1);
         }
     }
 }
