@@ -313,16 +313,39 @@ __device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         if (!((take_mask >> b) & 1u)) continue;
-        const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
         if constexpr (MODE == kModeKnn) {
+            // With inline codes the entry keeps the table position and the
+            // table (j + 1 in bits 41..49); resolve_ids_kernel turns it into
+            // the id after the search, off this kernel's critical path.
             const uint32_t p = base + before[b];
-            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(dist[b], cid);
+            const uint64_t e = lazy_id ? (static_cast<uint64_t>(j + 1) << kQueryShift) | pack_entry(dist[b], pos[b])
+                                       : pack_entry(dist[b], id[b]);
+            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = e;
         } else {
+            const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
             const uint64_t p = __ldg(a.out_base + q) + base + before[b];
             if (p < __ldg(a.out_base + q + 1))
                 a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(dist[b], cid);
             else
                 atomicExch(a.err, 1);
+        }
+    }
+}
+
+// Table positions stored by the k-NN search (inline codes) become ids: an
+// entry with a nonzero table tag t in bits 41..49 holds position p of table
+// t - 1, whose id is tables[t - 1].ids[p].  Only buffers that did not
+// overflow are read later, so only those are resolved.
+__global__ void resolve_ids_kernel(uint64_t* __restrict__ buf, const uint32_t* __restrict__ cnt, uint32_t cap,
+                                   uint32_t nq, const TableDesc* __restrict__ tables) {
+    for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        const uint32_t c = cnt[q];
+        if (c > cap) continue;
+        uint64_t* e = buf + static_cast<uint64_t>(q) * cap;
+        for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
+            const uint64_t v = e[i];
+            const uint32_t tag = static_cast<uint32_t>(v >> kQueryShift);
+            if (tag != 0) e[i] = (v & (0x1FFull << 32)) | __ldg(tables[tag - 1].ids + static_cast<uint32_t>(v));
         }
     }
 }
@@ -619,16 +642,25 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
 
 // ------------------------------------------------------- streamed slices
 // With inline codes every big-bucket slice is one contiguous run of codes.
-// Each warp streams its slices through two 4 KB shared-memory stages: lane 0
-// starts a bulk asynchronous copy (cp.async.bulk, completion counted on an
-// mbarrier) of the next stage while the warp verifies the current one.  Every
-// wait on an mbarrier is bounded; on expiry the kernel raises a.timeout,
-// waits (bounded) for its own copies still in flight and leaves.
+// Each warp streams its slices through a ring of kStages 4 KB shared-memory
+// stages: lane 0 keeps bulk asynchronous copies (cp.async.bulk, completion
+// counted on an mbarrier per stage) of the next kStages - 1 stages in flight
+// while the warp verifies the current one.  Every wait on an mbarrier is
+// bounded; on expiry the kernel raises a.timeout, waits (bounded) for its own
+// copies still in flight and leaves.
 #ifndef MIH_STAGE_BYTES
 #define MIH_STAGE_BYTES 4096
 #endif
+#ifndef MIH_STREAM_STAGES
+#define MIH_STREAM_STAGES 2
+#endif
+#ifndef MIH_STREAM_WARPS
+#define MIH_STREAM_WARPS 8
+#endif
 constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;
-constexpr int kStreamWarps = 8;
+constexpr int kStages = MIH_STREAM_STAGES;
+constexpr int kStreamWarps = MIH_STREAM_WARPS;
+static_assert(kStages >= 2 && kStages <= 4, "stage ring of 2 to 4 slots");
 constexpr uint32_t kWaitLimit = 1u << 24;
 constexpr uint32_t kStageSlot = kStageBytes + 16;   // + one 8-byte code of realignment (W = 1)
 
@@ -673,6 +705,7 @@ struct Stage {
     uint32_t pos, cnt, end;
     bool valid;
     int bnd, hd;
+    uint32_t shift;   // code offset of the stage inside its slot (W = 1 realigns to 16 bytes)
     Code<W> g;
 };
 
@@ -753,31 +786,38 @@ __device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage
     return shift;
 }
 
+// resident CTAs per SM the stage ring leaves room for (sets the register budget)
+#ifdef MIH_STREAM_MIN_BLOCKS
+constexpr int kStreamMinBlocks = MIH_STREAM_MIN_BLOCKS;
+#else
+constexpr int kStreamMinBlocks = (227 * 1024) / (kStreamWarps * kStages * (kStageBytes + 16) + 8 * 1024) > 0
+                                     ? (227 * 1024) / (kStreamWarps * kStages * (kStageBytes + 16) + 8 * 1024)
+                                     : 1;
+#endif
+
 template <int W, int MODE, bool ALIGNED>
-__global__ void __launch_bounds__(kStreamWarps * 32, 3) search_stream_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_stream_kernel(SearchArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_len[kMaxTables];
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
     __shared__ uint32_t s_hist[kStreamWarps][kHistBins];
-    __shared__ __align__(8) uint64_t s_bar[kStreamWarps][2];
+    __shared__ __align__(8) uint64_t s_bar[kStreamWarps][kStages];
     build_layout(a.tables, a.m, W, s_len, s_mask);
     for (int i = threadIdx.x; i < kStreamWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     if (lane == 0) {
-        mbar_init(&s_bar[warp][0], 1);
-        mbar_init(&s_bar[warp][1], 1);
+        for (int i = 0; i < kStages; ++i) mbar_init(&s_bar[warp][i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const Layout L{s_len, s_mask};
     uint32_t* whist = s_hist[warp];
-    // slot/barrier b of this warp (b = 0, 1), selected without indexing
-    // register arrays (which would put them in local memory)
-    unsigned char* const slot0 = dsm + (2 * warp) * kStageSlot;
+    // slot/barrier i of this warp, selected by arithmetic (no register arrays
+    // indexed at run time, which would live in local memory)
+    unsigned char* const slot0 = dsm + warp * kStages * kStageSlot;
     uint64_t* const bar0 = &s_bar[warp][0];
-    uint32_t parities = 0u;   // bit b: phase parity of barrier b
-    uint32_t shift0 = 0u, shift1 = 0u;
+    uint32_t parities = 0u;   // bit i: phase parity of barrier i
     const unsigned int count = min(*a.big_count, a.big_cap);
 
     SliceFeed feed;
@@ -789,11 +829,23 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 3) search_stream_kernel(Sea
     none.q = 0;
     none.t = 0;
     none.bnd = none.hd = 0;
+    none.shift = 0;
+    // the ring: cur (slot b), then up to kStages - 1 stages already issued
     Stage<W> cur = next_stage<W>(a, none, count, feed);
     if (!cur.valid) return;
-    shift0 = issue_stage<W>(a, cur, slot0, bar0);
-    Stage<W> nxt = next_stage<W>(a, cur, count, feed);
-    if (nxt.valid) shift1 = issue_stage<W>(a, nxt, slot0 + kStageSlot, bar0 + 1);
+    cur.shift = issue_stage<W>(a, cur, slot0, bar0);
+    Stage<W> n1 = next_stage<W>(a, cur, count, feed);
+    if (n1.valid) n1.shift = issue_stage<W>(a, n1, slot0 + kStageSlot, bar0 + 1);
+    Stage<W> n2 = n1;
+    if constexpr (kStages >= 3) {
+        n2 = next_stage<W>(a, n1, count, feed);
+        if (n2.valid) n2.shift = issue_stage<W>(a, n2, slot0 + 2 * kStageSlot, bar0 + 2);
+    }
+    Stage<W> n3 = n2;
+    if constexpr (kStages >= 4) {
+        n3 = next_stage<W>(a, n2, count, feed);
+        if (n3.valid) n3.shift = issue_stage<W>(a, n3, slot0 + 3 * kStageSlot, bar0 + 3);
+    }
     // entries per lane and batch (a 4 KB stage is 1, 2 or 4 batches for W = 4, 2, 1)
     constexpr int kPer = static_cast<int>(kStageBytes / (8 * W));
     constexpr int B = kPer / 32 < 4 ? kPer / 32 : 4;
@@ -804,14 +856,19 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 3) search_stream_kernel(Sea
         uint64_t* const bar_b = bar0 + b;
         if (!mbar_wait_bounded(bar_b, (parities >> b) & 1u)) {
             if (lane == 0) atomicExch(a.timeout, 1);
-            if (nxt.valid) mbar_wait_bounded(bar0 + (b ^ 1), (parities >> (b ^ 1)) & 1u);   // let our other copy land
+            // let this warp's other copies land before leaving
+            for (int i = 1; i < kStages; ++i) {
+                const bool issued = i == 1 ? n1.valid : (i == 2 ? n2.valid : n3.valid);
+                const int bi = (b + i) % kStages;
+                if (issued) mbar_wait_bounded(bar0 + bi, (parities >> bi) & 1u);
+            }
             return;
         }
         parities ^= 1u << b;
         // verify the stage out of shared memory
         const int j = cur.t % a.m, rho = cur.t / a.m;
         const CandSource src{nullptr, a.tables[j].ids, false};
-        const Code<W>* sc = reinterpret_cast<const Code<W>*>(slot_b) + (b ? shift1 : shift0);
+        const Code<W>* sc = reinterpret_cast<const Code<W>*>(slot_b) + cur.shift;
         uint32_t unused = 0;
         for (uint32_t base = 0; base < cur.cnt; base += 32 * B) {
             uint32_t pos[B], id[B];
@@ -832,14 +889,12 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 3) search_stream_kernel(Sea
                                                 valid, c, id, unique, unused);
         }
         __syncwarp();
-        // the slot just read takes the stage after next
-        const Stage<W> nn = next_stage<W>(a, nxt, count, feed);
-        if (nn.valid) {
-            const uint32_t sh = issue_stage<W>(a, nn, slot_b, bar_b);
-            if (b) shift1 = sh; else shift0 = sh;
-        }
+        // the slot just read takes the stage kStages after cur
+        const Stage<W>& last = kStages == 2 ? n1 : (kStages == 3 ? n2 : n3);
+        Stage<W> nn = next_stage<W>(a, last, count, feed);
+        if (nn.valid) nn.shift = issue_stage<W>(a, nn, slot_b, bar_b);
         // histogram and counters go out once the warp leaves this query
-        if (!nxt.valid || nxt.q != cur.q) {
+        if (!n1.valid || n1.q != cur.q) {
             if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(cur.q) * (a.q + 1), a.q);
             if (a.qstats) {
 #pragma unroll
@@ -848,13 +903,22 @@ __global__ void __launch_bounds__(kStreamWarps * 32, 3) search_stream_kernel(Sea
             }
             unique = 0;
         }
-        cur = nxt;
-        nxt = nn;
-        b ^= 1;
+        cur = n1;
+        if constexpr (kStages == 2) {
+            n1 = nn;
+        } else if constexpr (kStages == 3) {
+            n1 = n2;
+            n2 = nn;
+        } else {
+            n1 = n2;
+            n2 = n3;
+            n3 = nn;
+        }
+        b = (b + 1 == kStages) ? 0 : b + 1;
     }
 }
 
-size_t stream_smem_bytes() { return static_cast<size_t>(kStreamWarps) * 2 * kStageSlot; }
+size_t stream_smem_bytes() { return static_cast<size_t>(kStreamWarps) * kStages * kStageSlot; }
 
 // ------------------------------------------------------------ planning
 // Chunk count of each query's step range [t_lo, t_hi].
@@ -1784,6 +1848,11 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         ++waves;
         MIH_TRY(check_timeout(plan, s));
         MIH_TRY(check_flag(err, "mih_knn: second pass found more codes within d_k than counted", s));
+    }
+    if (ix->inline_codes && ix->n > 0) {
+        const unsigned blocks = nq < static_cast<uint32_t>(dev.sms) * 16u ? nq : static_cast<unsigned>(dev.sms) * 16u;
+        resolve_ids_kernel<<<blocks, 256, 0, s>>>(buf1, cnt1, cap, nq, ix->dev_tables);
+        MIH_LAUNCH_CHECK();
     }
 
     SelectInputs si;
