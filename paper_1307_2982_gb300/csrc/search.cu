@@ -661,7 +661,8 @@ constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;
 constexpr int kStages = MIH_STREAM_STAGES;
 constexpr int kStreamWarps = MIH_STREAM_WARPS;
 static_assert(kStages >= 2 && kStages <= 4, "stage ring of 2 to 4 slots");
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kWaitHintNs = 20000;          // longest suspension of one try_wait
+constexpr uint64_t kWaitNs = 1000000000ull;      // a bulk copy not done after 1 s is an error
 constexpr uint32_t kStageSlot = kStageBytes + 16;   // + one 8-byte code of realignment (W = 1)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -681,17 +682,32 @@ __device__ __forceinline__ void bulk_copy_to_smem(void* dst, const void* src, ui
                  : "memory");
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `bar` with the given parity.  Each try_wait may
+// suspend the warp (up to kWaitHintNs, woken early when the phase completes)
+// instead of spinning, so waiting warps leave the issue slots to the warps
+// that verify codes.  Gives up after kWaitNs of global time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
             : "memory");
         if (ok) return true;
+        if ((it & 63u) == 0) {
+            const uint64_t now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > kWaitNs) return false;
+        }
     }
-    return false;
 }
 
 // One stage: entries [pos, pos + cnt) of a slice ending at `end`, all of
