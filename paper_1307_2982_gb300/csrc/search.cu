@@ -507,24 +507,41 @@ __global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
         }
         lookup_buckets<kKeysPerLane>(tab, key, mine, bb, ee);
         uint32_t raw = 0, unique = 0;
+        // Big buckets go to the slice kernel.  The warp reserves the slices of
+        // all its big buckets with one atomic; if the list is full the
+        // reserved slots are marked empty and the warp scans those buckets here.
+        uint32_t ns_lane = 0;
+#pragma unroll
+        for (int r = 0; r < kKeysPerLane; ++r) {
+            const uint32_t sz = ee[r] - bb[r];
+            if (sz > kBigBucket) ns_lane += (sz + kSliceEntries - 1) / kSliceEntries;
+        }
+        const uint32_t ns_incl = warp_inclusive_scan(ns_lane);
+        const uint32_t ns_total = __shfl_sync(0xFFFFFFFFu, ns_incl, 31);
+        uint32_t at = 0;
+        bool fits = true;
+        if (ns_total != 0) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(a.big_count, ns_total);
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            at = base + ns_incl - ns_lane;
+            fits = static_cast<uint64_t>(base) + ns_total <= a.big_cap;
+        }
         int nz = 0;
         uint32_t tot = 0;
 #pragma unroll
         for (int r = 0; r < kKeysPerLane; ++r) {
             uint32_t sz = ee[r] - bb[r];
             if (sz > kBigBucket) {
-                // Hand the bucket to the slice kernel; if the list is full the
-                // reserved slots are marked empty and the warp scans it here.
                 const uint32_t ns = (sz + kSliceEntries - 1) / kSliceEntries;
-                const unsigned int at = atomicAdd(a.big_count, ns);
-                const bool fits = static_cast<uint64_t>(at) + ns <= a.big_cap;
-                for (uint32_t i = 0; i < ns && at + i < a.big_cap; ++i) {
+                for (uint32_t i = 0; i < ns; ++i, ++at) {
+                    if (at >= a.big_cap) continue;
                     BigSlice bs;
                     bs.q = fits ? q : kPadId;
                     bs.t = t;
                     bs.begin = bb[r] + i * kSliceEntries;
                     bs.end = min(ee[r], bs.begin + kSliceEntries);
-                    a.big[at + i] = bs;
+                    a.big[at] = bs;
                 }
                 if (fits) {
                     raw += sz;
@@ -730,9 +747,19 @@ struct Stage {
 // slice (fetched one slice ahead) and that slice's descriptor (loaded one
 // slice ahead): starting a slice uses only values already in registers.
 struct SliceFeed {
-    uint32_t next_idx;   // index of the slice after `ahead` (warp-uniform)
-    BigSlice ahead;      // descriptor of the next slice (q = kPadId past the end)
+    uint32_t grab;       // lane 0: first index of the pending grab (its atomic was
+                         // issued at least one slice ago; other lanes: unused)
+    uint32_t next_idx;   // first index of the current grab not yet loaded (warp-uniform)
+    uint32_t left;       // indices of the current grab not yet loaded (>= 1)
+    BigSlice ahead;      // descriptor of the slice the warp starts next (t < 0 past the end)
 };
+
+// Slice indices are taken kSliceGrab at a time, so the shared counter sees a
+// fraction of the warps' requests.
+#ifndef MIH_SLICE_GRAB
+#define MIH_SLICE_GRAB 2
+#endif
+constexpr uint32_t kSliceGrab = MIH_SLICE_GRAB;
 
 __device__ __forceinline__ BigSlice load_slice(const SearchArgs& a, uint32_t i, unsigned int count) {
     BigSlice bs;
@@ -743,10 +770,27 @@ __device__ __forceinline__ BigSlice load_slice(const SearchArgs& a, uint32_t i, 
     return bs;
 }
 
-__device__ __forceinline__ uint32_t fetch_slice_index(const SearchArgs& a) {
-    uint32_t i = 0;
-    if (lane_id() == 0) i = atomicAdd(a.big_next, 1u);
-    return __shfl_sync(0xFFFFFFFFu, i, 0);
+// Lane 0 starts the next grab; its result is read (broadcast) only when the
+// warp needs it, a slice later, so the atomic's latency stays hidden.
+__device__ __forceinline__ void start_grab(const SearchArgs& a, SliceFeed& feed) {
+    if (lane_id() == 0) feed.grab = atomicAdd(a.big_next, kSliceGrab);
+}
+
+__device__ __forceinline__ void take_grab(SliceFeed& feed) {
+    feed.next_idx = __shfl_sync(0xFFFFFFFFu, feed.grab, 0);
+    feed.left = kSliceGrab;
+}
+
+// Moves the feed one slice on: loads the descriptor of next_idx into `ahead`;
+// when the current grab runs out the pending grab becomes current and the
+// next one is started.  One grab is always pending.
+__device__ __forceinline__ void advance_feed(const SearchArgs& a, SliceFeed& feed, unsigned int count) {
+    feed.ahead = load_slice(a, feed.next_idx, count);
+    ++feed.next_idx;
+    if (--feed.left == 0) {
+        take_grab(feed);
+        start_grab(a, feed);
+    }
 }
 
 template <int W>
@@ -766,10 +810,9 @@ __device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<
             r.valid = false;
             return r;
         }
-        // refill the feed: descriptor of the index fetched a slice ago, and
-        // the index after it (both complete while this slice is verified)
-        feed.ahead = load_slice(a, feed.next_idx, count);
-        feed.next_idx = fetch_slice_index(a);
+        // refill the feed: the descriptor of the index known since the last
+        // slice (its load completes while this slice is verified)
+        advance_feed(a, feed, count);
         if (bs.q == kPadId) continue;   // reserved but never filled
         r.q = bs.q;
         r.t = bs.t;
@@ -837,8 +880,11 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
     const unsigned int count = min(*a.big_count, a.big_cap);
 
     SliceFeed feed;
-    feed.ahead = load_slice(a, fetch_slice_index(a), count);
-    feed.next_idx = fetch_slice_index(a);
+    feed.grab = 0;
+    start_grab(a, feed);
+    take_grab(feed);        // the first grab is waited for
+    start_grab(a, feed);    // the pending one
+    advance_feed(a, feed, count);
     Stage<W> none;
     none.valid = true;
     none.pos = none.cnt = none.end = 0;
