@@ -335,17 +335,22 @@ __device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout
 // Table positions stored by the k-NN search (inline codes) become ids: an
 // entry with a nonzero table tag t in bits 41..49 holds position p of table
 // t - 1, whose id is tables[t - 1].ids[p].  Only buffers that did not
-// overflow are read later, so only those are resolved.
+// overflow are read later, and of those only entries within d_k (the
+// selection reads no others), so only those are resolved.
 __global__ void resolve_ids_kernel(uint64_t* __restrict__ buf, const uint32_t* __restrict__ cnt, uint32_t cap,
-                                   uint32_t nq, const TableDesc* __restrict__ tables) {
+                                   uint32_t nq, const TableDesc* __restrict__ tables,
+                                   const int32_t* __restrict__ dk) {
     for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
         const uint32_t c = cnt[q];
         if (c > cap) continue;
+        const uint32_t dmax = static_cast<uint32_t>(dk[q]);
         uint64_t* e = buf + static_cast<uint64_t>(q) * cap;
         for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
             const uint64_t v = e[i];
             const uint32_t tag = static_cast<uint32_t>(v >> kQueryShift);
-            if (tag != 0) e[i] = (v & (0x1FFull << 32)) | __ldg(tables[tag - 1].ids + static_cast<uint32_t>(v));
+            const uint32_t d = static_cast<uint32_t>(v >> 32) & 0x1FFu;
+            if (tag != 0 && d <= dmax)
+                e[i] = (v & (0x1FFull << 32)) | __ldg(tables[tag - 1].ids + static_cast<uint32_t>(v));
         }
     }
 }
@@ -1913,7 +1918,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     }
     if (ix->inline_codes && ix->n > 0) {
         const unsigned blocks = nq < static_cast<uint32_t>(dev.sms) * 16u ? nq : static_cast<unsigned>(dev.sms) * 16u;
-        resolve_ids_kernel<<<blocks, 256, 0, s>>>(buf1, cnt1, cap, nq, ix->dev_tables);
+        resolve_ids_kernel<<<blocks, 256, 0, s>>>(buf1, cnt1, cap, nq, ix->dev_tables, dk);
         MIH_LAUNCH_CHECK();
     }
 
