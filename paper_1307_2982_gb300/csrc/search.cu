@@ -425,8 +425,14 @@ constexpr int kBigBatch = 8;   // candidates in flight per lane, big-bucket slic
 constexpr int kWarps = kSearchThreads / 32;
 constexpr int kHistBins = 257; // distances 0..256
 
+// resident CTAs per SM asked of the chunk kernel (its chunks are latency-bound:
+// more warps in flight, more chunks per second)
+#ifndef MIH_SEARCH_MIN_BLOCKS
+#define MIH_SEARCH_MIN_BLOCKS 4
+#endif
+
 template <int W, int MODE, bool ALIGNED>
-__global__ void __launch_bounds__(kSearchThreads) search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_kernel(SearchArgs a) {
     __shared__ int s_off[kMaxTables];
     __shared__ int s_len[kMaxTables];
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
