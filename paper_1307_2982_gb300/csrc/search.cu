@@ -1439,6 +1439,10 @@ mih_status launch_search(const SearchArgs& a, int W, const DeviceInfo& dev, cuda
     return launch_search_w<4, MODE>(a, dev, s, launch);
 }
 
+#ifndef MIH_BIG_CAP_LOG2
+#define MIH_BIG_CAP_LOG2 25
+#endif
+
 // Per-launch work state (chunk offsets, counters, big list).
 struct Plan {
     uint64_t* chunk_off = nullptr;           // [nq + 1]
@@ -1452,7 +1456,11 @@ struct Plan {
 mih_status plan_alloc(Plan& p, uint32_t nq, Workspace& ws) {
     MIH_TRY(ws.alloc(&p.chunk_off, static_cast<size_t>(nq) + 1));
     MIH_TRY(ws.alloc(&p.counters, 2));
-    p.big_cap = 1u << 22;
+    // Slice descriptors per wave (16 B each).  A wave over many medium buckets
+    // (1e9 uniform 64-bit codes, 21-bit substrings: ~500 codes per bucket)
+    // makes ten million slices or more; a bucket whose slices do not fit is
+    // scanned by the chunk kernel's warp itself, which is far slower.
+    p.big_cap = 1u << MIH_BIG_CAP_LOG2;
     MIH_TRY(ws.alloc(&p.big, p.big_cap));
     MIH_TRY(ws.alloc(&p.timeout, 1));
     MIH_CUDA(cudaMemsetAsync(p.timeout, 0, sizeof(int), ws.stream()));
