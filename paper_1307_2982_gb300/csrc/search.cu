@@ -421,7 +421,10 @@ __device__ __forceinline__ void lookup_buckets(const TableDesc& t, const uint32_
 }
 
 constexpr int kBatch = 4;      // candidates in flight per lane, bucket unions
-constexpr int kBigBatch = 8;   // candidates in flight per lane, big-bucket slices
+#ifndef MIH_BIG_BATCH
+#define MIH_BIG_BATCH 8
+#endif
+constexpr int kBigBatch = MIH_BIG_BATCH;   // candidates in flight per lane, big-bucket slices
 constexpr int kWarps = kSearchThreads / 32;
 constexpr int kHistBins = 257; // distances 0..256
 
@@ -622,9 +625,64 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
     }
 }
 
+// Slices are taken from the wave's list through a shared counter.  To keep
+// that round trip off the critical path each warp holds the index of its next
+// slice (fetched one slice ahead) and that slice's descriptor (loaded one
+// slice ahead): starting a slice uses only values already in registers.
+struct SliceFeed {
+    uint32_t grab;       // lane 0: first index of the pending grab (its atomic was
+                         // issued at least one slice ago; other lanes: unused)
+    uint32_t next_idx;   // first index of the current grab not yet loaded (warp-uniform)
+    uint32_t left;       // indices of the current grab not yet loaded (>= 1)
+    BigSlice ahead;      // descriptor of the slice the warp starts next (t < 0 past the end)
+};
+
+// Slice indices are taken kSliceGrab at a time, so the shared counter sees a
+// fraction of the warps' requests.
+#ifndef MIH_SLICE_GRAB
+#define MIH_SLICE_GRAB 2
+#endif
+constexpr uint32_t kSliceGrab = MIH_SLICE_GRAB;
+
+__device__ __forceinline__ BigSlice load_slice(const SearchArgs& a, uint32_t i, unsigned int count) {
+    BigSlice bs;
+    bs.q = kPadId;
+    bs.t = -1;
+    bs.begin = bs.end = 0;
+    if (i < count) bs = a.big[i];
+    return bs;
+}
+
+// Lane 0 starts the next grab; its result is read (broadcast) only when the
+// warp needs it, a slice later, so the atomic's latency stays hidden.
+__device__ __forceinline__ void start_grab(const SearchArgs& a, SliceFeed& feed) {
+    if (lane_id() == 0) feed.grab = atomicAdd(a.big_next, kSliceGrab);
+}
+
+__device__ __forceinline__ void take_grab(SliceFeed& feed) {
+    feed.next_idx = __shfl_sync(0xFFFFFFFFu, feed.grab, 0);
+    feed.left = kSliceGrab;
+}
+
+// Moves the feed one slice on: loads the descriptor of next_idx into `ahead`;
+// when the current grab runs out the pending grab becomes current and the
+// next one is started.  One grab is always pending.
+__device__ __forceinline__ void advance_feed(const SearchArgs& a, SliceFeed& feed, unsigned int count) {
+    feed.ahead = load_slice(a, feed.next_idx, count);
+    ++feed.next_idx;
+    if (--feed.left == 0) {
+        take_grab(feed);
+        start_grab(a, feed);
+    }
+}
+
 // Slices of large buckets, one warp per slice, 32 * kBigBatch entries per round.
+#ifndef MIH_BIG_MIN_BLOCKS
+#define MIH_BIG_MIN_BLOCKS 1
+#endif
+
 template <int W, int MODE, bool ALIGNED>
-__global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kSearchThreads, MIH_BIG_MIN_BLOCKS) search_big_kernel(SearchArgs a) {
     __shared__ int s_len[kMaxTables];
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
     __shared__ uint32_t s_hist[kWarps][kHistBins];
@@ -635,12 +693,16 @@ __global__ void __launch_bounds__(kSearchThreads) search_big_kernel(SearchArgs a
     const uint32_t lane = lane_id();
     uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned int count = min(*a.big_count, a.big_cap);
+    SliceFeed feed;
+    feed.grab = 0;
+    start_grab(a, feed);
+    take_grab(feed);        // the first grab is waited for
+    start_grab(a, feed);    // the pending one
+    advance_feed(a, feed, count);
     for (;;) {
-        unsigned int i = 0;
-        if (lane == 0) i = atomicAdd(a.big_next, 1u);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= count) break;
-        const BigSlice bs = a.big[i];
+        const BigSlice bs = feed.ahead;
+        if (bs.t < 0) break;              // the list is exhausted
+        advance_feed(a, feed, count);     // the next descriptor loads while this slice runs
         if (bs.q == kPadId) continue;
         const int j = bs.t % a.m, rho = bs.t / a.m;
         const Code<W> g = load_query<W>(a.queries, bs.q);
@@ -752,57 +814,6 @@ struct Stage {
     uint32_t shift;   // code offset of the stage inside its slot (W = 1 realigns to 16 bytes)
     Code<W> g;
 };
-
-// Slices are taken from the wave's list through a shared counter.  To keep
-// that round trip off the critical path each warp holds the index of its next
-// slice (fetched one slice ahead) and that slice's descriptor (loaded one
-// slice ahead): starting a slice uses only values already in registers.
-struct SliceFeed {
-    uint32_t grab;       // lane 0: first index of the pending grab (its atomic was
-                         // issued at least one slice ago; other lanes: unused)
-    uint32_t next_idx;   // first index of the current grab not yet loaded (warp-uniform)
-    uint32_t left;       // indices of the current grab not yet loaded (>= 1)
-    BigSlice ahead;      // descriptor of the slice the warp starts next (t < 0 past the end)
-};
-
-// Slice indices are taken kSliceGrab at a time, so the shared counter sees a
-// fraction of the warps' requests.
-#ifndef MIH_SLICE_GRAB
-#define MIH_SLICE_GRAB 2
-#endif
-constexpr uint32_t kSliceGrab = MIH_SLICE_GRAB;
-
-__device__ __forceinline__ BigSlice load_slice(const SearchArgs& a, uint32_t i, unsigned int count) {
-    BigSlice bs;
-    bs.q = kPadId;
-    bs.t = -1;
-    bs.begin = bs.end = 0;
-    if (i < count) bs = a.big[i];
-    return bs;
-}
-
-// Lane 0 starts the next grab; its result is read (broadcast) only when the
-// warp needs it, a slice later, so the atomic's latency stays hidden.
-__device__ __forceinline__ void start_grab(const SearchArgs& a, SliceFeed& feed) {
-    if (lane_id() == 0) feed.grab = atomicAdd(a.big_next, kSliceGrab);
-}
-
-__device__ __forceinline__ void take_grab(SliceFeed& feed) {
-    feed.next_idx = __shfl_sync(0xFFFFFFFFu, feed.grab, 0);
-    feed.left = kSliceGrab;
-}
-
-// Moves the feed one slice on: loads the descriptor of next_idx into `ahead`;
-// when the current grab runs out the pending grab becomes current and the
-// next one is started.  One grab is always pending.
-__device__ __forceinline__ void advance_feed(const SearchArgs& a, SliceFeed& feed, unsigned int count) {
-    feed.ahead = load_slice(a, feed.next_idx, count);
-    ++feed.next_idx;
-    if (--feed.left == 0) {
-        take_grab(feed);
-        start_grab(a, feed);
-    }
-}
 
 template <int W>
 __device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<W>& st, unsigned int count,
