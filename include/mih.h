@@ -89,7 +89,20 @@ typedef struct {
                               waves; MIH_EXEC_HOST = a host loop that reads the
                               number of active queries after every wave.
                               0 = MIH_EXEC_AUTO (the graph). */
-    int32_t reserved[11];  /* must be zero */
+    int32_t pad_;          /* must be zero */
+    const int32_t *bit_order; /* Sec. 5.5 "Substring Optimization": NULL = the
+                              consecutive substrings of Sec. 2.1.  Otherwise a
+                              host array of q distinct bit indices, read during
+                              mih_build only: bit p of the code the tables see is
+                              bit bit_order[p] of the stored code, so substring j
+                              takes bits bit_order[o_j .. o_j + s_j - 1] (o_j, s_j
+                              of mih_substring_layout).  Results are unchanged
+                              (a common permutation of the bits keeps every
+                              Hamming distance); the index then holds a permuted
+                              copy of the codes (n * q/8 bytes) and permutes each
+                              batch of queries.  mih_greedy_substrings computes
+                              the paper's greedy order. */
+    int32_t reserved[8];   /* must be zero */
 } mih_params;
 
 /* mih_params.executor (not part of the paper: a launch strategy). */
@@ -296,6 +309,34 @@ MIH_API double mih_cost_model(int q, uint64_t n, int s, int r);
 /* Number of substrings suggested by Sec. 3.1 / Table 4: the integer closest
  * to q / log2(n), clamped so that no substring exceeds 32 bits and m <= q. */
 MIH_API int mih_suggest_m(int q, uint64_t n);
+
+/* Greedy assignment of bits to substrings from their correlation (Sec. 5.5
+ * "Substring Optimization").  corr: host double[q][q], row-major, the
+ * correlation between bits a and b (mih_bit_correlation; only |corr| is
+ * used).  The first substring takes bit (seed mod q); substring j = 1..m-1
+ * then takes the unused bit most correlated with the bit substring j-1 took.
+ * Then, visiting the substrings in turn and skipping full ones, substring j
+ * takes the unused bit whose largest correlation with the bits it already
+ * holds is smallest.  Ties go to the lower bit index.  Substring sizes are
+ * those of mih_substring_layout.  Writes bit_order[q] (host) in the format
+ * of mih_params.bit_order: the bits of substring j in the order taken.
+ * Errors: MIH_EINVAL for q not in {64, 128, 256}, m < 1, m > q, NULL
+ * pointers. */
+MIH_API mih_status mih_greedy_substrings(const double *corr, int q, int m, uint64_t seed, int32_t *bit_order);
+
+/* ------------------------------------------------------------------------
+ * mih_bit_correlation -- the correlation between every pair of the q bits
+ * over n sample codes (Sec. 5.5 uses 10M codes), computed on the GPU from
+ * bit-plane AND-popcounts: corr[a][b] = (n c_ab - c_a c_b) /
+ * sqrt(c_a (n - c_a) c_b (n - c_b)), where c_a counts the codes with bit a
+ * set and c_ab those with both; 0 where a bit is constant.  The diagonal
+ * is 1 (0 for a constant bit).
+ *
+ * codes   device, uint64[n][q/64], 16-byte aligned for q >= 128; 1 <= n <= 2^32 - 1.
+ * corr    host, double[q][q], written before return (the call synchronises
+ *         its stream).
+ * Errors: MIH_EINVAL (q, n, pointers), MIH_ENOMEM, MIH_ECUDA. */
+MIH_API mih_status mih_bit_correlation(const uint64_t *codes, uint64_t n, int q, double *corr, void *stream);
 
 /* ------------------------------------------------------------------------
  * Per-call profile of the calling host thread (not part of the paper).

@@ -16,6 +16,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmih.so")
 _lib = None
@@ -30,7 +32,7 @@ EXPORTS = (
     "mih_build", "mih_free", "mih_index_get_info", "mih_knn", "mih_rnear", "linscan_knn",
     "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
-    "mih_autotune",
+    "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation",
 )
 
 
@@ -43,7 +45,8 @@ class MihError(RuntimeError):
 class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
                 ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("executor", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 11)]
+                ("pad_", ctypes.c_int32), ("bit_order", ctypes.POINTER(ctypes.c_int32)),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class mih_stats(ctypes.Structure):
@@ -118,6 +121,10 @@ def load():
     lib.mih_set_timing.restype = None
     lib.mih_last_profile.argtypes = [P]
     lib.mih_last_profile.restype = st
+    lib.mih_greedy_substrings.argtypes = [P, i32, i32, u64, P]
+    lib.mih_greedy_substrings.restype = st
+    lib.mih_bit_correlation.argtypes = [P, u64, i32, P, P]
+    lib.mih_bit_correlation.restype = st
     _lib = lib
     return lib
 
@@ -192,6 +199,31 @@ def mih_suggest_m(q: int, n: int) -> int:
     return int(load().mih_suggest_m(q, n))
 
 
+def mih_greedy_substrings(corr, m: int, seed: int = 0):
+    """Greedy bit-to-substring assignment of Sec. 5.5 from a (q, q) correlation
+    matrix; returns the int32 bit order for ``mih_build(bit_order=...)``."""
+    c = np.ascontiguousarray(corr, dtype=np.float64)
+    q = c.shape[0]
+    if c.shape != (q, q):
+        raise ValueError("corr must be square")
+    out = np.empty(q, dtype=np.int32)
+    _check(load().mih_greedy_substrings(c.ctypes.data, q, m, seed, out.ctypes.data), "mih_greedy_substrings")
+    return out
+
+
+def mih_bit_correlation(codes, q: int, stream=None):
+    """(q, q) float64 correlation between the bits of the device codes (Sec. 5.5)."""
+    ptr, n = _codes_arg(codes, q)
+    out = np.empty((q, q), dtype=np.float64)
+    _check(load().mih_bit_correlation(ptr, n, q, out.ctypes.data, _stream(stream)), "mih_bit_correlation")
+    return out
+
+
+def optimize_substrings(sample_codes, q: int, m: int, seed: int = 0, stream=None):
+    """Bit order of optimised substrings (Sec. 5.5) from sample codes on the device."""
+    return mih_greedy_substrings(mih_bit_correlation(sample_codes, q, stream=stream), m, seed)
+
+
 # ------------------------------------------------------------------- index
 class MihIndex:
     """Owns a ``mih_index*``; keeps the borrowed code tensor alive."""
@@ -229,7 +261,8 @@ class MihIndex:
 
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
-              inline_codes: int = 0, probe: int = 0, executor: int = MIH_EXEC_AUTO, stream=None) -> MihIndex:
+              inline_codes: int = 0, probe: int = 0, executor: int = MIH_EXEC_AUTO, bit_order=None,
+              stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
@@ -237,6 +270,11 @@ def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_fact
     p.inline_codes = inline_codes
     p.probe = probe
     p.executor = executor
+    if bit_order is not None:
+        order = np.ascontiguousarray(bit_order, dtype=np.int32)
+        if order.shape != (q,):
+            raise ValueError("bit_order must hold q entries")
+        p.bit_order = order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)

@@ -16,6 +16,7 @@
 
 #include "index.h"
 #include "launch.h"
+#include "substrings.h"
 
 namespace mih {
 namespace {
@@ -304,11 +305,12 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     }
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
-        for (int i = 0; i < 11; ++i)
-            if (params->reserved[i] != 0) {
-                set_error("mih_build: params.reserved must be zero");
+        for (int i = 0; i < 8; ++i)
+            if (params->reserved[i] != 0 || params->pad_ != 0) {
+                set_error("mih_build: params.reserved and params.pad_ must be zero");
                 return MIH_EINVAL;
             }
+        if (params->bit_order) MIH_TRY(check_bit_order(params->bit_order, q));
         if (params->executor < MIH_EXEC_AUTO || params->executor > MIH_EXEC_GRAPH) {
             set_error("mih_build: unknown executor %d", params->executor);
             return MIH_EINVAL;
@@ -341,6 +343,29 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->scan_factor = params ? params->scan_factor : 0;
     ix->probe = (!params || params->probe == 0) ? 1024 : (params->probe < 0 ? 0 : params->probe);
     ix->executor = params ? params->executor : MIH_EXEC_AUTO;
+    if (params && params->bit_order) {
+        // Optimised substrings (Sec. 5.5): the tables see codes whose bits are
+        // permuted; the index keeps that copy and the order for the queries.
+        mih_status pst = index_alloc(ix, reinterpret_cast<void**>(&ix->bit_order), q * sizeof(int32_t));
+        uint64_t* perm = nullptr;
+        if (pst == MIH_OK)
+            pst = index_alloc(ix, reinterpret_cast<void**>(&perm), static_cast<size_t>(n) * (q / 64) * 8 + 16);
+        if (pst == MIH_OK) {
+            const cudaError_t e = cudaMemcpyAsync(ix->bit_order, params->bit_order, q * sizeof(int32_t),
+                                                  cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                set_error("mih_build: bit order upload failed: %s", cudaGetErrorString(e));
+                pst = MIH_ECUDA;
+            }
+        }
+        if (pst == MIH_OK) pst = permute_codes(codes, perm, n, q, ix->bit_order, s);
+        if (pst == MIH_OK) pst = cudaStreamSynchronize(s) == cudaSuccess ? MIH_OK : MIH_ECUDA;
+        if (pst != MIH_OK) {
+            mih_free(ix);
+            return pst;
+        }
+        ix->codes = perm;
+    }
     {
         // Inline codes: m * n * q/8 bytes on top of ids (4 m n) and tables;
         // automatic when the whole index fits in half the free memory.

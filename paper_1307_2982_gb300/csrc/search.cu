@@ -32,6 +32,7 @@
 #include "index.h"
 #include "launch.h"
 #include "search.h"
+#include "substrings.h"
 
 namespace mih {
 namespace {
@@ -1631,6 +1632,17 @@ mih_status validate_common(const mih_index* ix, const uint64_t* queries, uint32_
     return MIH_OK;
 }
 
+// With optimised substrings the index searches bit-permuted codes: the
+// queries get the same permutation, in scratch memory, before any kernel.
+mih_status permute_queries(const mih_index* ix, const uint64_t** queries, uint32_t nq, Workspace& ws) {
+    if (!ix->bit_order) return MIH_OK;
+    uint64_t* qp;
+    MIH_TRY(ws.alloc(&qp, static_cast<size_t>(nq) * ix->W));
+    MIH_TRY(permute_codes(*queries, qp, nq, ix->q, ix->bit_order, ws.stream()));
+    *queries = qp;
+    return MIH_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- exported
@@ -1785,6 +1797,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_TRY(device_info(&dev));
     const int qb = ix->q;
     const uint32_t cap = knn_buffer_cap(kmax, nq);
+    MIH_TRY(permute_queries(ix, &queries, nq, ws));
 
     int32_t *t_lo, *t_hi, *bound, *dk;
     uint32_t *hist, *cnt1;
@@ -2009,6 +2022,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
     MIH_TRY(device_info(&dev));
     const int qb = ix->q;
     const int reff = r < qb ? r : qb;  // every code lies within q bits
+    if (nq > 0) MIH_TRY(permute_queries(ix, &queries, nq, ws));
     int32_t *t_lo, *t_hi, *bound;
     uint32_t* cnt;
     unsigned long long* qstats;
