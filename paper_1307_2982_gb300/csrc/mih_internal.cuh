@@ -14,7 +14,10 @@ constexpr uint32_t kPadId = 0xFFFFFFFFu;
 constexpr uint32_t kEmptySlot = 0xFFFFFFFFu;
 constexpr int kChunkKeys = 256;          // ring keys per work chunk (one warp)
 constexpr int kKeysPerLane = kChunkKeys / 32;
-constexpr uint32_t kBigBucket = 64;      // buckets above this go to the slice list
+#ifndef MIH_BIG_BUCKET
+#define MIH_BIG_BUCKET 64
+#endif
+constexpr uint32_t kBigBucket = MIH_BIG_BUCKET;   // buckets above this go to the slice list
 
 // ---------------------------------------------------------------- tables
 // One substring hash table (Sec. 6): either direct-addressed CSR offsets over

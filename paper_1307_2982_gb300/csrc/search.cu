@@ -1024,6 +1024,70 @@ __global__ void plan_chunks_kernel(const TableDesc* __restrict__ tables, int m, 
     }
 }
 
+// Chunks of query q's step range (0 when idle), as plan_chunks_kernel counts them.
+__device__ __forceinline__ uint64_t query_chunks(const int* s_len, int m, uint64_t n, const int32_t* t_lo,
+                                                 const int32_t* t_hi, const uint8_t* exh, uint32_t q) {
+    uint64_t c = 0;
+    if (t_lo[q] <= t_hi[q]) {
+        if (exh && exh[q]) c = (n + kScanChunk - 1) / kScanChunk;
+        else
+            for (int t = t_lo[q]; t <= t_hi[q]; ++t) c += step_chunks(s_len, m, t);
+    }
+    return c;
+}
+
+// One CTA plans a whole wave when nq is small enough: chunk counts, their
+// exclusive scan into chunk_off[0..nq] and the zeroed work counters, in one
+// launch instead of a count kernel, a multi-kernel scan and a memset.
+constexpr int kPlanThreads = 1024;
+constexpr uint32_t kPlanOneBlockMax = 64u * kPlanThreads;   // nq + 1 entries at most
+
+__global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(const TableDesc* __restrict__ tables, int m,
+                                                                 uint32_t nq, uint64_t n,
+                                                                 const int32_t* __restrict__ t_lo,
+                                                                 const int32_t* __restrict__ t_hi,
+                                                                 const uint8_t* __restrict__ exh,
+                                                                 uint64_t* __restrict__ chunk_off,
+                                                                 unsigned long long* __restrict__ counters) {
+    __shared__ int s_len[kMaxTables];
+    __shared__ unsigned long long s_warp[kPlanThreads / 32];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
+    if (threadIdx.x < 2) counters[threadIdx.x] = 0ull;
+    __syncthreads();
+    // thread i owns queries [i * per, (i + 1) * per)
+    const uint32_t per = (nq + kPlanThreads - 1) / kPlanThreads;
+    const uint32_t q0 = threadIdx.x * per;
+    const uint32_t q1 = min(nq, q0 + per);
+    unsigned long long sum = 0;
+    for (uint32_t q = q0; q < q1; ++q) sum += query_chunks(s_len, m, n, t_lo, t_hi, exh, q);
+    // block exclusive scan of the per-thread sums
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    unsigned long long incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (static_cast<int>(lane) >= o) incl += v;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (static_cast<int>(lane) >= o) w += v;
+        }
+        s_warp[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    unsigned long long run = (warp > 0 ? s_warp[warp - 1] : 0ull) + incl - sum;
+    for (uint32_t q = q0; q < q1; ++q) {
+        chunk_off[q] = run;
+        run += query_chunks(s_len, m, n, t_lo, t_hi, exh, q);
+    }
+    if (threadIdx.x == kPlanThreads - 1) chunk_off[nq] = s_warp[kPlanThreads / 32 - 1];
+}
+
 // Lookups of steps t0..t1 (sum of ring sizes, Eq. 1 per table).
 __device__ __forceinline__ uint64_t steps_lookups(const int* s_len, int m, int t0, int t1) {
     uint64_t l = 0;
@@ -1500,12 +1564,20 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
                     const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr) {
     const bool in_graph = cs != nullptr;
     cudaStream_t s = in_graph ? cs : ws.stream();
-    plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
-                                                      p.chunk_off);
-    MIH_LAUNCH_CHECK();
-    if (in_graph) MIH_TRY(scan_exclusive_u64_pre(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, p.scan_tmp, s));
-    else MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
-    MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
+    if (static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
+        plan_scan_kernel<<<1, kPlanThreads, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
+                                                    p.chunk_off, p.counters);
+        MIH_LAUNCH_CHECK();
+    } else {
+        plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
+                                                          p.chunk_off);
+        MIH_LAUNCH_CHECK();
+        if (in_graph)
+            MIH_TRY(scan_exclusive_u64_pre(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, p.scan_tmp, s));
+        else
+            MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
+        MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
+    }
     a.t_lo = t_lo;
     a.t_hi = t_hi;
     a.chunk_off = p.chunk_off;
