@@ -385,8 +385,13 @@ def run_ours(a):
     # ---- roofline of the dominant kernel (fused MIH search), algorithmic bytes
     sparse = [kd == mih.MIH_TABLE_SPARSE for kd in info["table_kind"]]
     bytes_per_lookup = 8 + (8 if all(sparse) else 0)       # bucket bounds (+ one {key, rank} slot)
-    # full code per candidate; the id too unless the tables keep codes inline
-    bytes_per_cand = q // 8 + (0 if info["inline_codes"] else 4)
+    # full code per candidate; the id too unless the tables keep codes inline.
+    # When every substring is one 32-bit word (m = q/32) the inline records
+    # leave out the table's own word (its distance is the ring radius).
+    if info["inline_codes"]:
+        bytes_per_cand = q // 8 - (4 if m == q // 32 else 0)
+    else:
+        bytes_per_cand = q // 8 + 4
     alg_bytes = stats_acc["lookups"] * bytes_per_lookup + stats_acc["candidates_raw"] * bytes_per_cand
     peaks = {}
     try:

@@ -53,6 +53,27 @@ __global__ void gather_codes_kernel(const uint64_t* __restrict__ codes, const ui
     }
 }
 
+// Inline records of table j when every substring is one 32-bit word: the
+// code's 2W words except word j, in order (the table's key fixes word j up to
+// the ring: its distance to the query's word is the ring radius).
+template <int W>
+__global__ void gather_records_kernel(const uint64_t* __restrict__ codes, const uint32_t* __restrict__ ids,
+                                      uint64_t n, int j, uint32_t* __restrict__ out) {
+    constexpr int R = 2 * W - 1;
+    for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const Code<W> c = load_code<W>(codes, __ldg(ids + p));
+        uint32_t w32[2 * W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            w32[2 * w] = static_cast<uint32_t>(c.w[w]);
+            w32[2 * w + 1] = static_cast<uint32_t>(c.w[w] >> 32);
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) out[p * R + i] = w32[i < j ? i : i + 1];
+    }
+}
+
 __global__ void count_keys_kernel(const uint32_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ counts) {
     for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
@@ -189,7 +210,20 @@ mih_status build_table(mih_index* ix, int j, int kind, const DeviceInfo& dev, cu
     t.ids = ids;
     t.kind = kind;
     t.codes = nullptr;
-    if (ix->inline_codes && n > 0) {
+    t.rec_words = 0;
+    if (ix->inline_codes && n > 0 && ix->m == 2 * ix->W) {
+        // every substring is one 32-bit word: records without the table's own word
+        const int R = 2 * ix->W - 1;
+        uint32_t* rec;
+        // 16 bytes of padding: streamed copies are widened to 16-byte boundaries
+        MIH_TRY(index_alloc(ix, reinterpret_cast<void**>(&rec), n * R * sizeof(uint32_t) + 16));
+        if (ix->W == 1) gather_records_kernel<1><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, j, rec);
+        else if (ix->W == 2) gather_records_kernel<2><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, j, rec);
+        else gather_records_kernel<4><<<grid_for(n, dev.sms), 256, 0, s>>>(ix->codes, ids, n, j, rec);
+        MIH_LAUNCH_CHECK();
+        t.codes = reinterpret_cast<const uint64_t*>(rec);
+        t.rec_words = R;
+    } else if (ix->inline_codes && n > 0) {
         uint64_t* inl;
         // 16 bytes of padding: streamed copies of 8-byte codes are widened to
         // 16-byte boundaries and may read one code past the end
@@ -378,9 +412,11 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
                 cudaGetLastError();
                 free_b = 0;
             }
-            // ids (4 B) + inline codes (q/8 B) per entry and table, plus the
-            // build's transient key/id buffers (12 B per code)
-            const double est = static_cast<double>(m) * n * (q / 8 + 4) + 12.0 * n;
+            // ids (4 B) + inline codes (q/8 B, 4 B less when every substring
+            // is one 32-bit word) per entry and table, plus the build's
+            // transient key/id buffers (12 B per code)
+            const int rec_b = (m == 2 * (q / 64)) ? q / 8 - 4 : q / 8;
+            const double est = static_cast<double>(m) * n * (rec_b + 4) + 12.0 * n;
             ix->inline_codes = est < 0.6 * static_cast<double>(free_b);
         }
     }

@@ -27,14 +27,16 @@ struct TableDesc {
     int32_t off;        // first code bit of the substring
     int32_t len;        // s_j (1..32)
     int32_t kind;       // MIH_TABLE_DIRECT / MIH_TABLE_SPARSE
-    int32_t pad_;
+    int32_t rec_words;  // inline records of this many 32-bit words: the code without the
+                        // table's own word (every substring one 32-bit word); 0 = full codes
     const uint32_t* ids;       // n ids ordered by (key, id)
     const uint32_t* offsets;   // direct: offsets[2^s + 1]; sparse: begins[U + 1]
     const uint2* slots;        // sparse: 4 * nbuckets slots {key, rank}
     uint64_t bucket_mask;      // sparse: nbuckets - 1 (power of two)
     uint32_t max_probe;        // sparse: longest probe sequence at build
     uint32_t pad2_;
-    const uint64_t* codes;     // optional: codes in the order of `ids` (W words each)
+    const uint64_t* codes;     // optional: codes in the order of `ids`: W uint64 words each, or
+                               // (rec_words > 0) records of rec_words uint32 words
 };
 
 // ---------------------------------------------------------------- binomials

@@ -258,40 +258,16 @@ __device__ __forceinline__ void handle_batch(const SearchArgs& a, const Layout& 
                                         unique_acc, raw_acc);
 }
 
-// The second half of handle_batch, for codes already in registers (from
-// global memory or from a shared-memory stage).  id[b] is the candidate's id
-// unless the source keeps codes inline (then ids are read only when stored).
-template <int W, int MODE, bool ALIGNED, int B>
-__device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout& L, uint32_t* whist, uint32_t q,
-                                               int j, int rho, int t_done, int hist_done, int bnd, const Code<W>& g,
-                                               const CandSource& src, const uint32_t (&pos)[B],
-                                               const bool (&valid)[B], const Code<W> (&c)[B],
-                                               const uint32_t (&id)[B], uint32_t& unique_acc, uint32_t& raw_acc) {
-    const bool lazy_id = !src.by_id && src.ids != nullptr;
-    const int far = (bnd < 0 || a.exact_stats) ? 0x7FFFFFFF : bnd;
+// Stores (k-NN), collects or counts the taken candidates of a warp batch:
+// bit b of take_mask marks candidate b of the lane.  One atomic reserves the
+// slots of the whole warp batch.  With lazy ids (inline codes) a k-NN entry
+// keeps the table position and the table (j + 1 in bits 41..49).
+template <int MODE, int B>
+__device__ __forceinline__ void store_batch(const SearchArgs& a, uint32_t q, int j, bool lazy_id,
+                                            const uint32_t* ids, const uint32_t (&pos)[B], const uint32_t (&id)[B],
+                                            const int (&dist)[B], uint32_t take_mask) {
     const uint32_t lane = lane_id();
     const uint32_t lt = (1u << lane) - 1u;
-    // Distances and tests of all B candidates first; the kept entries of the
-    // batch then take one slot reservation (a single atomic) for the warp.
-    int dist[B];
-    uint32_t take_mask = 0;   // bit b: candidate b is stored / collected
-#pragma unroll
-    for (int b = 0; b < B; ++b) {
-        int d = 0;
-        bool keep = false, count = false;
-        if (valid[b]) eval_candidate<W, ALIGNED>(a.m, L, j, rho, t_done, hist_done, far, g, c[b], d, keep, count);
-        dist[b] = d;
-        if (j < 0) raw_acc += (valid[b] && count) ? 1u : 0u;
-        if constexpr (MODE == kModeKnn) {
-            if (keep && count) {
-                atomicAdd(&whist[d], 1u);
-                ++unique_acc;
-            }
-        } else {
-            unique_acc += keep ? 1u : 0u;
-        }
-        if (keep && d <= bnd) take_mask |= 1u << b;
-    }
     if constexpr (MODE == kModeCount) {
         const uint32_t mine = __popc(take_mask);
         const uint32_t total = __reduce_add_sync(0xFFFFFFFFu, mine);
@@ -323,7 +299,7 @@ __device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout
                                        : pack_entry(dist[b], id[b]);
             if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = e;
         } else {
-            const uint32_t cid = lazy_id ? __ldg(src.ids + pos[b]) : id[b];
+            const uint32_t cid = lazy_id ? __ldg(ids + pos[b]) : id[b];
             const uint64_t p = __ldg(a.out_base + q) + base + before[b];
             if (p < __ldg(a.out_base + q + 1))
                 a.buf[p] = (static_cast<uint64_t>(q) << kQueryShift) | pack_entry(dist[b], cid);
@@ -331,6 +307,86 @@ __device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout
                 atomicExch(a.err, 1);
         }
     }
+}
+
+
+// The second half of handle_batch, for codes already in registers (from
+// global memory or from a shared-memory stage).  id[b] is the candidate's id
+// unless the source keeps codes inline (then ids are read only when stored).
+template <int W, int MODE, bool ALIGNED, int B>
+__device__ __forceinline__ void process_loaded(const SearchArgs& a, const Layout& L, uint32_t* whist, uint32_t q,
+                                               int j, int rho, int t_done, int hist_done, int bnd, const Code<W>& g,
+                                               const CandSource& src, const uint32_t (&pos)[B],
+                                               const bool (&valid)[B], const Code<W> (&c)[B],
+                                               const uint32_t (&id)[B], uint32_t& unique_acc, uint32_t& raw_acc) {
+    const bool lazy_id = !src.by_id && src.ids != nullptr;
+    const int far = (bnd < 0 || a.exact_stats) ? 0x7FFFFFFF : bnd;
+    // Distances and tests of all B candidates first; the kept entries of the
+    // batch then take one slot reservation (a single atomic) for the warp.
+    int dist[B];
+    uint32_t take_mask = 0;   // bit b: candidate b is stored / collected
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        int d = 0;
+        bool keep = false, count = false;
+        if (valid[b]) eval_candidate<W, ALIGNED>(a.m, L, j, rho, t_done, hist_done, far, g, c[b], d, keep, count);
+        dist[b] = d;
+        if (j < 0) raw_acc += (valid[b] && count) ? 1u : 0u;
+        if constexpr (MODE == kModeKnn) {
+            if (keep && count) {
+                atomicAdd(&whist[d], 1u);
+                ++unique_acc;
+            }
+        } else {
+            unique_acc += keep ? 1u : 0u;
+        }
+        if (keep && d <= bnd) take_mask |= 1u << b;
+    }
+    store_batch<MODE, B>(a, q, j, lazy_id, src.ids, pos, id, dist, take_mask);
+}
+
+// process_loaded for inline records without the table's own word (every
+// substring one 32-bit word): record word i is code word i (i < j) or i + 1
+// (i >= j), gq holds the query's words in the same order, and the table's own
+// word differs from the query's in exactly rho bits (the ring).  The
+// first-discoverer test (reading c8) keeps the code when no earlier table is
+// within rho bits and no later one within rho - 1: word i needs at least
+// th[i] = rho + (i < j) differing bits.
+template <int R, int MODE, int B>
+__device__ __forceinline__ void process_records(const SearchArgs& a, uint32_t* whist, uint32_t q, int j, int rho,
+                                                int bnd, bool count_new, const uint32_t (&gq)[R],
+                                                const uint32_t (&th)[R], const uint32_t* ids,
+                                                const uint32_t (&pos)[B], const bool (&valid)[B],
+                                                const uint32_t (&rec)[B][R], uint32_t& unique_acc) {
+    const int far = (bnd < 0 || a.exact_stats) ? 0x7FFFFFFF : bnd;
+    int dist[B];
+    uint32_t take_mask = 0;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        int d = rho;
+        int pc[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            pc[i] = __popc(rec[b][i] ^ gq[i]);
+            d += pc[i];
+        }
+        dist[b] = d;
+        if (valid[b] && d <= far) {
+            bool keep = true;
+#pragma unroll
+            for (int i = 0; i < R; ++i) keep = keep && static_cast<uint32_t>(pc[i]) >= th[i];
+            if constexpr (MODE == kModeKnn) {
+                if (keep && count_new) {
+                    atomicAdd(&whist[d], 1u);
+                    ++unique_acc;
+                }
+            } else {
+                unique_acc += keep ? 1u : 0u;
+            }
+            if (keep && d <= bnd) take_mask |= 1u << b;
+        }
+    }
+    store_batch<MODE, B>(a, q, j, true, ids, pos, pos, dist, take_mask);
 }
 
 // Table positions stored by the k-NN search (inline codes) become ids: an
@@ -512,7 +568,9 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
         const Code<W> g = load_query<W>(a.queries, q);
         const uint32_t gkey = substring_bits<W>(g, s_off[j], s);
         const TableDesc& tab = a.tables[j];
-        const CandSource src = tab.codes ? CandSource{tab.codes, tab.ids, false} : CandSource{a.codes, tab.ids, true};
+        // whole inline codes, else (no inline codes, or records) the codes by id
+        const CandSource src = (tab.codes && tab.rec_words == 0) ? CandSource{tab.codes, tab.ids, false}
+                                                                 : CandSource{a.codes, tab.ids, true};
         uint64_t x = mine > 0 ? unrank_subset(first, s, rho) : 0ull;
         uint32_t key[kKeysPerLane], bb[kKeysPerLane], ee[kKeysPerLane];
 #pragma unroll
@@ -708,7 +766,8 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_BIG_MIN_BLOCKS) search_big
         const int j = bs.t % a.m, rho = bs.t / a.m;
         const Code<W> g = load_query<W>(a.queries, bs.q);
         const TableDesc& tab = a.tables[j];
-        const CandSource src = tab.codes ? CandSource{tab.codes, tab.ids, false} : CandSource{a.codes, tab.ids, true};
+        const CandSource src = (tab.codes && tab.rec_words == 0) ? CandSource{tab.codes, tab.ids, false}
+                                                                 : CandSource{a.codes, tab.ids, true};
         const int hd = a.hist_done ? __ldg(a.hist_done + bs.q) : -1;
         const int bnd = __ldg(a.bound + bs.q);
         uint32_t unique = 0, unused = 0;
@@ -816,10 +875,17 @@ struct Stage {
     Code<W> g;
 };
 
-template <int W>
+// Entries per stage: whole codes (W uint64 words), or records of 2W - 1
+// uint32 words (REDUCED), rounded down to whole warp rows.
+template <int W, bool REDUCED>
+__host__ __device__ constexpr uint32_t stage_entries() {
+    return REDUCED ? ((kStageBytes / (4 * (2 * W - 1))) & ~31u) : kStageBytes / (8 * W);
+}
+
+template <int W, bool REDUCED>
 __device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<W>& st, unsigned int count,
                                                SliceFeed& feed) {
-    constexpr uint32_t kPer = kStageBytes / (8 * W);
+    constexpr uint32_t kPer = stage_entries<W, REDUCED>();
     Stage<W> r = st;
     if (!st.valid) return r;
     if (st.pos + st.cnt < st.end) {
@@ -849,21 +915,30 @@ __device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<
     }
 }
 
-// Lane 0 starts the copy of stage st into slot `buf`; returns the code offset
-// of the stage inside the slot (nonzero only when W = 1 realigns to 16 bytes).
-template <int W>
+// Lane 0 starts the copy of stage st into slot `buf`; returns the entry
+// offset of the stage inside the slot: the copy starts on a 16-byte boundary,
+// so W = 1 codes realign by up to one code and REDUCED records by up to three.
+template <int W, bool REDUCED>
 __device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage<W>& st, unsigned char* buf,
                                                 uint64_t* bar) {
-    const uint64_t* codes = a.tables[st.t % a.m].codes;
+    const unsigned char* base = reinterpret_cast<const unsigned char*>(a.tables[st.t % a.m].codes);
     uint32_t lo = st.pos, shift = 0, bytes = st.cnt * 8u * W;
-    if constexpr (W == 1) {
+    uint64_t src_off = static_cast<uint64_t>(st.pos) * 8u * W;
+    if constexpr (REDUCED) {
+        constexpr uint32_t rb = 4u * (2 * W - 1);   // record bytes; 4 records are 16 R bytes
+        lo = st.pos & ~3u;
+        shift = st.pos - lo;
+        bytes = ((st.cnt + shift) * rb + 15u) & ~15u;   // the table keeps 16 bytes of padding
+        src_off = static_cast<uint64_t>(lo) * rb;
+    } else if constexpr (W == 1) {
         lo = st.pos & ~1u;
         shift = st.pos - lo;
         bytes = ((st.cnt + shift) * 8u + 15u) & ~15u;   // the table keeps 16 bytes of padding
+        src_off = static_cast<uint64_t>(lo) * 8u;
     }
     if (lane_id() == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads of the slot are done
-        bulk_copy_to_smem(buf, codes + static_cast<uint64_t>(lo) * W, bytes, bar);
+        bulk_copy_to_smem(buf, base + src_off, bytes, bar);
     }
     return shift;
 }
@@ -879,6 +954,9 @@ constexpr int kStreamMinBlocks = (227 * 1024) / (kStreamWarps * kStages * (kStag
 
 template <int W, int MODE, bool ALIGNED>
 __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_stream_kernel(SearchArgs a) {
+    // aligned tables (every substring one 32-bit word) keep inline records
+    // without their own word; the others keep whole codes
+    constexpr bool REDUCED = ALIGNED;
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ int s_len[kMaxTables];
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
@@ -916,24 +994,27 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
     none.bnd = none.hd = 0;
     none.shift = 0;
     // the ring: cur (slot b), then up to kStages - 1 stages already issued
-    Stage<W> cur = next_stage<W>(a, none, count, feed);
+    Stage<W> cur = next_stage<W, REDUCED>(a, none, count, feed);
     if (!cur.valid) return;
-    cur.shift = issue_stage<W>(a, cur, slot0, bar0);
-    Stage<W> n1 = next_stage<W>(a, cur, count, feed);
-    if (n1.valid) n1.shift = issue_stage<W>(a, n1, slot0 + kStageSlot, bar0 + 1);
+    cur.shift = issue_stage<W, REDUCED>(a, cur, slot0, bar0);
+    Stage<W> n1 = next_stage<W, REDUCED>(a, cur, count, feed);
+    if (n1.valid) n1.shift = issue_stage<W, REDUCED>(a, n1, slot0 + kStageSlot, bar0 + 1);
     Stage<W> n2 = n1;
     if constexpr (kStages >= 3) {
-        n2 = next_stage<W>(a, n1, count, feed);
-        if (n2.valid) n2.shift = issue_stage<W>(a, n2, slot0 + 2 * kStageSlot, bar0 + 2);
+        n2 = next_stage<W, REDUCED>(a, n1, count, feed);
+        if (n2.valid) n2.shift = issue_stage<W, REDUCED>(a, n2, slot0 + 2 * kStageSlot, bar0 + 2);
     }
     Stage<W> n3 = n2;
     if constexpr (kStages >= 4) {
-        n3 = next_stage<W>(a, n2, count, feed);
-        if (n3.valid) n3.shift = issue_stage<W>(a, n3, slot0 + 3 * kStageSlot, bar0 + 3);
+        n3 = next_stage<W, REDUCED>(a, n2, count, feed);
+        if (n3.valid) n3.shift = issue_stage<W, REDUCED>(a, n3, slot0 + 3 * kStageSlot, bar0 + 3);
     }
-    // entries per lane and batch (a 4 KB stage is 1, 2 or 4 batches for W = 4, 2, 1)
-    constexpr int kPer = static_cast<int>(kStageBytes / (8 * W));
+    // entries per lane and batch: whole codes, B of them per lane at a time
+    // (a 4 KB stage is 1, 2 or 4 batches for W = 4, 2, 1), or records
+    constexpr int kPer = static_cast<int>(stage_entries<W, REDUCED>());
     constexpr int B = kPer / 32 < 4 ? kPer / 32 : 4;
+    constexpr int R = 2 * W - 1;
+    constexpr int BR = REDUCED && W == 1 ? 8 : 4;   // records per lane at a time
     int b = 0;
     uint32_t unique = 0;
     while (cur.valid) {
@@ -952,6 +1033,37 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
         parities ^= 1u << b;
         // verify the stage out of shared memory
         const int j = cur.t % a.m, rho = cur.t / a.m;
+        if constexpr (REDUCED) {
+            uint32_t g32[2 * W], gq[R], th[R];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                g32[2 * w] = static_cast<uint32_t>(cur.g.w[w]);
+                g32[2 * w + 1] = static_cast<uint32_t>(cur.g.w[w] >> 32);
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                gq[i] = i < j ? g32[i] : g32[i + 1];
+                th[i] = static_cast<uint32_t>(rho) + (i < j ? 1u : 0u);
+            }
+            const bool count_new = 2 * W * rho + j > cur.hd;
+            const uint32_t* sr = reinterpret_cast<const uint32_t*>(slot_b) + cur.shift * R;
+            const uint32_t* ids = a.tables[j].ids;
+            for (uint32_t base = 0; base < cur.cnt; base += 32 * BR) {
+                uint32_t pos[BR];
+                bool valid[BR];
+                uint32_t rec[BR][R];
+#pragma unroll
+                for (int k = 0; k < BR; ++k) {
+                    const uint32_t i = base + k * 32 + lane;
+                    valid[k] = i < cur.cnt;
+                    pos[k] = cur.pos + i;
+#pragma unroll
+                    for (int w = 0; w < R; ++w) rec[k][w] = valid[k] ? sr[i * R + w] : 0u;
+                }
+                process_records<R, MODE, BR>(a, whist, cur.q, j, rho, cur.bnd, count_new, gq, th, ids, pos, valid,
+                                             rec, unique);
+            }
+        } else {
         const CandSource src{nullptr, a.tables[j].ids, false};
         const Code<W>* sc = reinterpret_cast<const Code<W>*>(slot_b) + cur.shift;
         uint32_t unused = 0;
@@ -973,11 +1085,12 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
             process_loaded<W, MODE, ALIGNED, B>(a, L, whist, cur.q, j, rho, -1, cur.hd, cur.bnd, cur.g, src, pos,
                                                 valid, c, id, unique, unused);
         }
+        }
         __syncwarp();
         // the slot just read takes the stage kStages after cur
         const Stage<W>& last = kStages == 2 ? n1 : (kStages == 3 ? n2 : n3);
-        Stage<W> nn = next_stage<W>(a, last, count, feed);
-        if (nn.valid) nn.shift = issue_stage<W>(a, nn, slot_b, bar_b);
+        Stage<W> nn = next_stage<W, REDUCED>(a, last, count, feed);
+        if (nn.valid) nn.shift = issue_stage<W, REDUCED>(a, nn, slot_b, bar_b);
         // histogram and counters go out once the warp leaves this query
         if (!n1.valid || n1.q != cur.q) {
             if (MODE == kModeKnn) flush_hist(whist, a.hist + static_cast<uint64_t>(cur.q) * (a.q + 1), a.q);
@@ -1385,7 +1498,8 @@ __global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __res
         e = __shfl_sync(0xFFFFFFFFu, e, 0);
         const uint32_t end = min(e, b + probe);
         for (uint32_t p = b + lane; p < end; p += 32) {
-            const Code<W> c = t.codes ? load_code<W>(t.codes, p) : load_code<W>(codes, __ldg(t.ids + p));
+            const Code<W> c = (t.codes && t.rec_words == 0) ? load_code<W>(t.codes, p)
+                                                            : load_code<W>(codes, __ldg(t.ids + p));
             // a code also filed under the query's key in an earlier table is
             // counted there or not at all: the count never exceeds the number
             // of distinct codes, so the bound stays valid
