@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -113,7 +114,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples: a temporary file unless MIH_BENCH_CLOCKS_CSV names one to keep
+        self.path = os.environ.get("MIH_BENCH_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"mih_clocks_rank{gpu_index}_{os.getpid()}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
