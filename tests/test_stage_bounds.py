@@ -1,0 +1,46 @@
+"""Bounds of the slice kernel's bulk copies, checked on the host for every
+entry layout: each copy starts and ends on 16-byte boundaries, covers the
+stage's entries, fits its 4112-byte shared-memory slot, and reads at most 16
+bytes past the last entry (the padding the build adds after each table's
+inline codes).  The arithmetic restates the kernel's stage sizing (4 KB
+stages: 8W-byte codes, or 4(2W-1)-byte records rounded down to whole warp
+rows) so that a change to one is checked against the other by review."""
+import numpy as np
+import pytest
+
+STAGE, SLOT = 4096, 4096 + 16
+
+
+def stage_entries(W, reduced):
+    return ((STAGE // (4 * (2 * W - 1))) & ~31) if reduced else STAGE // (8 * W)
+
+
+def copy_of(W, reduced, pos, cnt):
+    """(first byte, bytes, entry offset in the slot) of the copy of entries [pos, pos + cnt)."""
+    if reduced:
+        rb = 4 * (2 * W - 1)
+        lo = pos & ~3
+        return lo * rb, ((cnt + pos - lo) * rb + 15) & ~15, pos - lo, rb
+    if W == 1:
+        lo = pos & ~1
+        return lo * 8, ((cnt + pos - lo) * 8 + 15) & ~15, pos - lo, 8
+    return pos * 8 * W, cnt * 8 * W, 0, 8 * W
+
+
+@pytest.mark.parametrize("W,reduced", [(1, False), (2, False), (4, False), (1, True), (2, True), (4, True)])
+def test_stage_copies_stay_in_bounds(W, reduced):
+    rng = np.random.default_rng(W * 10 + reduced)
+    per = stage_entries(W, reduced)
+    assert per % 32 == 0 and per > 0
+    for n in (1, 2, 3, 5, 97, 1024, 100_003):
+        for _ in range(300):
+            pos = int(rng.integers(0, n))
+            cnt = int(rng.integers(1, min(per, n - pos) + 1))
+            start, nbytes, shift, eb = copy_of(W, reduced, pos, cnt)
+            assert start % 16 == 0 and nbytes % 16 == 0 and nbytes > 0
+            assert nbytes <= SLOT
+            # the stage's entries lie inside the copy
+            assert start <= pos * eb and (pos + cnt) * eb <= start + nbytes
+            assert shift * eb == pos * eb - start
+            # at most 16 bytes past the end of the table's n entries
+            assert start + nbytes <= n * eb + 16
