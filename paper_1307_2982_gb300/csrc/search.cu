@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "index.h"
@@ -1578,23 +1579,42 @@ struct GridCfg {
 };
 
 template <int W, int MODE, bool ALIGNED>
+mih_status init_search_cfg(GridCfg* cfg) {
+    int v = 0, w = 0, x = 0;
+    const size_t smem = stream_smem_bytes();
+    MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE, ALIGNED>, kSearchThreads, 0));
+    MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, search_big_kernel<W, MODE, ALIGNED>, kSearchThreads,
+                                                           0));
+    MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+    MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, search_stream_kernel<W, MODE, ALIGNED>,
+                                                           kStreamWarps * 32, smem));
+    cfg->bps_big = w > 0 ? w : 1;
+    cfg->bps_stream = x > 0 ? x : 1;
+    cfg->bps = v > 0 ? v : 1;
+    return MIH_OK;
+}
+
+// Once per device and kernel variant (the shared-memory attribute is a
+// per-device setting), safe when several host threads search at once.
+template <int W, int MODE, bool ALIGNED>
 mih_status search_cfg(const GridCfg** out) {
-    static GridCfg cfg;
-    if (cfg.bps == 0) {
-        int v = 0, w = 0, x = 0;
-        const size_t smem = stream_smem_bytes();
-        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE, ALIGNED>, kSearchThreads, 0));
-        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, search_big_kernel<W, MODE, ALIGNED>, kSearchThreads,
-                                                               0));
-        MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-        MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, search_stream_kernel<W, MODE, ALIGNED>,
-                                                               kStreamWarps * 32, smem));
-        cfg.bps_big = w > 0 ? w : 1;
-        cfg.bps_stream = x > 0 ? x : 1;
-        cfg.bps = v > 0 ? v : 1;
+    constexpr int kDevs = 64;
+    static GridCfg cfg[kDevs];
+    static std::once_flag once[kDevs];
+    static mih_status st[kDevs];
+    int d = 0;
+    MIH_CUDA(cudaGetDevice(&d));
+    if (d < 0 || d >= kDevs) {
+        set_error("device ordinal %d out of range", d);
+        return MIH_EINVAL;
     }
-    *out = &cfg;
+    std::call_once(once[d], [d] { st[d] = init_search_cfg<W, MODE, ALIGNED>(&cfg[d]); });
+    if (st[d] != MIH_OK) {
+        set_error("search kernel launch configuration failed on device %d", d);
+        return st[d];
+    }
+    *out = &cfg[d];
     return MIH_OK;
 }
 
