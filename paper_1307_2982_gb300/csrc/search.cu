@@ -39,7 +39,26 @@ namespace mih {
 namespace {
 
 constexpr int kSearchThreads = 256;
-constexpr uint32_t kSliceEntries = 1024;   // big-bucket slice
+constexpr uint32_t kSliceEntries = 1024;   // big-bucket slice of whole codes
+#ifndef MIH_STAGE_BYTES
+#define MIH_STAGE_BYTES 4096
+#endif
+constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;   // one shared-memory stage of the slice kernel
+
+// Entries per stage of the slice kernel: whole codes (W uint64 words), or
+// records of 2W - 1 uint32 words (inline records, every substring one 32-bit
+// word), rounded down to whole warp rows.
+template <int W, bool REDUCED>
+__host__ __device__ constexpr uint32_t stage_entries() {
+    return REDUCED ? ((kStageBytes / (4 * (2 * W - 1))) & ~31u) : kStageBytes / (8 * W);
+}
+
+// Entries per big-bucket slice: 1024 whole codes, or four full stages of
+// records, so that no slice ends in a nearly empty stage.
+template <int W, bool ALIGNED>
+__host__ __device__ constexpr uint32_t slice_entries() {
+    return ALIGNED ? 4u * stage_entries<W, true>() : kSliceEntries;
+}
 constexpr uint32_t kScanChunk = 4096;      // codes per chunk of a full verification pass
 constexpr int kQueryShift = 41;            // composite entry: q << 41 | d << 32 | id
 constexpr uint64_t kEntryMask = (1ull << kQueryShift) - 1ull;
@@ -507,6 +526,7 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
     const uint32_t lane = lane_id();
     uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned long long total_chunks = a.chunk_off[a.nq];
+    constexpr uint32_t kSlice = slice_entries<W, ALIGNED>();
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(a.chunk_next, 1ull);
@@ -588,7 +608,7 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
 #pragma unroll
         for (int r = 0; r < kKeysPerLane; ++r) {
             const uint32_t sz = ee[r] - bb[r];
-            if (sz > kBigBucket) ns_lane += (sz + kSliceEntries - 1) / kSliceEntries;
+            if (sz > kBigBucket) ns_lane += (sz + kSlice - 1) / kSlice;
         }
         const uint32_t ns_incl = warp_inclusive_scan(ns_lane);
         const uint32_t ns_total = __shfl_sync(0xFFFFFFFFu, ns_incl, 31);
@@ -607,14 +627,14 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
         for (int r = 0; r < kKeysPerLane; ++r) {
             uint32_t sz = ee[r] - bb[r];
             if (sz > kBigBucket) {
-                const uint32_t ns = (sz + kSliceEntries - 1) / kSliceEntries;
+                const uint32_t ns = (sz + kSlice - 1) / kSlice;
                 for (uint32_t i = 0; i < ns; ++i, ++at) {
                     if (at >= a.big_cap) continue;
                     BigSlice bs;
                     bs.q = fits ? q : kPadId;
                     bs.t = t;
-                    bs.begin = bb[r] + i * kSliceEntries;
-                    bs.end = min(ee[r], bs.begin + kSliceEntries);
+                    bs.begin = bb[r] + i * kSlice;
+                    bs.end = min(ee[r], bs.begin + kSlice);
                     a.big[at] = bs;
                 }
                 if (fits) {
@@ -799,16 +819,12 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_BIG_MIN_BLOCKS) search_big
 // while the warp verifies the current one.  Every wait on an mbarrier is
 // bounded; on expiry the kernel raises a.timeout, waits (bounded) for its own
 // copies still in flight and leaves.
-#ifndef MIH_STAGE_BYTES
-#define MIH_STAGE_BYTES 4096
-#endif
 #ifndef MIH_STREAM_STAGES
 #define MIH_STREAM_STAGES 2
 #endif
 #ifndef MIH_STREAM_WARPS
 #define MIH_STREAM_WARPS 8
 #endif
-constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;
 constexpr int kStages = MIH_STREAM_STAGES;
 constexpr int kStreamWarps = MIH_STREAM_WARPS;
 static_assert(kStages >= 2 && kStages <= 4, "stage ring of 2 to 4 slots");
@@ -875,13 +891,6 @@ struct Stage {
     uint32_t shift;   // code offset of the stage inside its slot (W = 1 realigns to 16 bytes)
     Code<W> g;
 };
-
-// Entries per stage: whole codes (W uint64 words), or records of 2W - 1
-// uint32 words (REDUCED), rounded down to whole warp rows.
-template <int W, bool REDUCED>
-__host__ __device__ constexpr uint32_t stage_entries() {
-    return REDUCED ? ((kStageBytes / (4 * (2 * W - 1))) & ~31u) : kStageBytes / (8 * W);
-}
 
 template <int W, bool REDUCED>
 __device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<W>& st, unsigned int count,
