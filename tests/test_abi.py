@@ -76,6 +76,26 @@ def test_cost_model_eq7(lib):
     assert lib.mih_cost_model(64, 10, 0, 3) < 0
 
 
+def test_cost_model_respects_eq8_and_eq9(lib):
+    """The paper's bounds on Eq. 7: cost(s) <= (1 + n/2^s)(q/s) 2^{H(r/q) s} (Eq. 8, r/q <= 1/2,
+    the entropy bound on a Hamming ball), and at s = log2 n, cost <= 2 (q/log2 n) n^{H(r/q)} (Eq. 9)."""
+    from math import log2
+
+    def H(x):
+        return 0.0 if x in (0.0, 1.0) else -x * log2(x) - (1 - x) * log2(1 - x)
+
+    for q in (64, 128, 256):
+        for s in (8, 16, 20, 24, 32):
+            for r in range(0, q // 2 + 1, 3):
+                n = 10**7
+                bound = (1 + n / 2**s) * (q / s) * 2 ** (H(r / q) * s)
+                assert lib.mih_cost_model(q, n, s, r) <= bound * (1 + 1e-12), (q, s, r)
+        for s in (16, 20, 24, 30):
+            n = 2**s                                    # s = log2 n exactly
+            for r in range(0, q // 2 + 1, 5):
+                assert lib.mih_cost_model(q, n, s, r) <= 2 * (q / s) * n ** H(r / q) * (1 + 1e-12), (q, s, r)
+
+
 def test_suggest_m_table4(lib):
     """Table 4: the selected m is usually the integer closest to q / log2(n)."""
     from test_oracle_pins import golden
