@@ -190,13 +190,25 @@ class MihOracle:
 
     ``counters`` of each search: lookups (buckets examined), raw candidates
     (bucket entries read), unique candidates, last step executed.
+
+    ``lengths`` (optional, m entries summing to q) gives table j the
+    contiguous substring of lengths[j] bits that follows table j-1's, the
+    per-table lengths the Conclusion (Sec. 8) leaves open; Propositions 1 and 2
+    (Sec. 2.1) hold for any partition of the bits into m disjoint substrings.
+    Default: the floor/ceil layout of the Sec. 2.1 footnote.
     """
 
-    def __init__(self, codes, q: int, m: int):
+    def __init__(self, codes, q: int, m: int, lengths=None):
         self.codes = _codes(codes)
         self.n, self.W = self.codes.shape
         self.q, self.m = q, m
-        self.off, self.len = substring_layout(q, m)
+        if lengths is None:
+            self.off, self.len = substring_layout(q, m)
+        else:
+            self.len = np.ascontiguousarray(lengths, dtype=np.int32)
+            if self.len.shape != (m,) or int(self.len.sum()) != q or int(self.len.min()) < 1:
+                raise ValueError("lengths must be m positive entries summing to q")
+            self.off = np.concatenate([[0], np.cumsum(self.len)[:-1]]).astype(np.int32)
         if int(self.len.max()) > 64:
             raise ValueError("oracle substring keys hold at most 64 bits")
         self.keys, self.ids = [], []

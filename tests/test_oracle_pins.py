@@ -243,6 +243,79 @@ def test_propositions_exhaustive_10bit(orc):
                 assert np.all((sub[:, :r + 1] == 0).any(axis=1)[within])
 
 
+# partitions of 10 bits into m contiguous substrings of unequal lengths
+UNEVEN_10 = [[7, 3], [1, 9], [2, 5, 3], [1, 1, 8], [4, 1, 1, 4], [3, 3, 2, 1, 1], [1, 2, 3, 4]]
+
+
+def test_propositions_exhaustive_10bit_uneven():
+    """Props 1 and 2 for substrings of unequal lengths (any disjoint partition)."""
+    q = 10
+    x = np.arange(2**q)
+    pc = np.array([bin(v).count("1") for v in range(2**q)])
+    for ln in UNEVEN_10:
+        m = len(ln)
+        off = np.concatenate([[0], np.cumsum(ln)[:-1]])
+        sub = np.stack([np.array([bin((int(v) >> int(o)) & ((1 << int(l)) - 1)).count("1") for v in x])
+                        for o, l in zip(off, ln)], axis=1)
+        for r in range(0, q + 1):
+            rp, a = r // m, r - m * (r // m)
+            within = pc <= r
+            assert np.all((sub <= rp).any(axis=1)[within]), (ln, r)
+            p2 = (sub[:, :a + 1] <= rp).any(axis=1) | (sub[:, a + 1:] <= rp - 1).any(axis=1)
+            assert np.all(p2[within]), (ln, r)
+
+
+def test_alg2_exhaustive_10bit_uneven(orc):
+    """Algorithm 2 with per-table lengths on the complete 10-bit space equals the definition."""
+    q = 10
+    db = np.arange(2**q, dtype=np.uint64).reshape(-1, 1)
+    qs = np.array([[0], [0b1011001110], [1023], [0b0000011111]], dtype=np.uint64)
+    for ln in UNEVEN_10:
+        mo = orc.MihOracle(db, q, len(ln), lengths=ln)
+        assert list(mo.off) == list(np.concatenate([[0], np.cumsum(ln)[:-1]]))
+        for r in range(0, q + 1):
+            off, wid, wd = orc.rnear(db, qs, r)
+            for i in range(len(qs)):
+                ids, dist, cnt = mo.rnear(qs[i], r)
+                assert np.array_equal(ids, wid[off[i]:off[i + 1]]), (ln, r, i)
+                assert np.array_equal(dist, wd[off[i]:off[i + 1]])
+
+
+@pytest.mark.parametrize("kind,q,ln,n", [
+    ("near", 64, [40, 24], 2000), ("uniform", 64, [10, 22, 32], 2500), ("ties", 128, [32, 32, 16, 24, 24], 1500),
+    ("near", 128, [20, 30, 26, 26, 26], 1500), ("near", 256, [32, 28, 28, 28, 28, 28, 28, 28, 28], 1000),
+])
+def test_alg3_uneven_lengths_equals_definition(orc, kind, q, ln, n):
+    """Algorithm 3 with per-table lengths: results are the definition's and the
+    counters match the independent derivation over the same partition."""
+    m = len(ln)
+    db = make_db(kind, q, n, 61)
+    fresh = make_db(kind, q, 5, 62) if kind != "ties" else perturb(db[5:10], 6, 62)
+    qs = np.concatenate([fresh, db[:2]])
+    mo = orc.MihOracle(db, q, m, lengths=ln)
+    off = np.concatenate([[0], np.cumsum(ln)[:-1]])
+    checked = 0
+    for k in [1, 10, 100]:
+        wid, wd = orc.knn(db, qs, k)
+        for i in range(len(qs)):
+            dk = int(wd[i][min(k, n) - 1])
+            want = alg3_expected_counts(db, qs[i], q, m, off, ln, dk)
+            if want[0] > LOOKUP_BUDGET:
+                continue
+            ids, dist, cnt = mo.knn(qs[i], k)
+            assert np.array_equal(ids, wid[i]) and np.array_equal(dist, wd[i]), (k, i)
+            assert cnt[3] == dk and tuple(cnt[:3]) == want, (k, i, cnt, want)
+            checked += 1
+    assert checked >= 6
+
+
+def test_oracle_rejects_bad_lengths(orc):
+    db = synth.uniform_codes(10, 64, 0)
+    for ln in ([32, 31], [64, 0], [33, 31, 0]):
+        with pytest.raises(ValueError):
+            orc.MihOracle(db, 64, len(ln), lengths=ln)
+
+
 def test_prop1_golden_examples(orc):
     rng = np.random.default_rng(5)
     for r, m, rp in golden("prop1_example"):
