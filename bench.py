@@ -194,22 +194,26 @@ def source_sha256() -> str:
     return h.hexdigest()
 
 
-def traffic_ratio():
-    """DRAM bytes per algorithmic byte of the search kernels, from the committed
-    ncu summary, if the kernels have not changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "search_kernels_5e7x128_traffic.txt")
+def slice_traffic(info, slice_launches, bstats, steps, q, kind, n, m):
+    """DRAM bytes per launch of the slice kernel from the committed ncu
+    summary (dram__bytes_read.sum + dram__bytes_write.sum over the slice
+    kernel's launches of one batch on the same workload), if the kernel
+    sources still hash as they did when it was captured; else (None, None)."""
+    path = os.path.join(ROOT, "profiles", "search_stream_1Bx128_k100_dram.txt")
     try:
         kv = {}
         with open(path) as f:
             for line in f:
-                if "=" in line and line.split("=")[0].strip() in ("traffic_per_algorithmic_byte", "source_sha256"):
+                if "=" in line:
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("source_sha256") == source_sha256():
-            return float(kv["traffic_per_algorithmic_byte"])
+        same = (kv.get("source_sha256") == source_sha256() and int(kv.get("n", -1)) == n and
+                int(kv.get("q", -1)) == q and int(kv.get("m", -1)) == m and kv.get("codes") == kind)
+        if same:
+            return float(kv["dram_bytes_per_launch"]), os.path.relpath(path, ROOT)
     except (OSError, ValueError, KeyError):
         pass
-    return None
+    return None, None
 
 
 # -------------------------------------------------------------- CPU oracle
@@ -364,7 +368,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats_acc = {"lookups": 0, "candidates_raw": 0, "candidates_unique": 0, "steps": 0, "phase2_queries": 0,
-                 "waves": 0}
+                 "waves": 0, "candidates_sliced": 0}
     main_ms, main_launches, launches = 0.0, 0, 0
     e0.record()
     for _ in range(a.steps):
@@ -385,7 +389,28 @@ def run_ours(a):
     ms_per_step = ms / a.steps
     value = world * nq * a.steps / (ms / 1000.0)
 
-    # ---- roofline of the dominant kernel (fused MIH search), algorithmic bytes
+    # ---- per-kernel breakdown: a few more batches with an event pair around
+    # every launch (the waves then run from a host loop: same kernels and
+    # results, no graph), outside the timed region
+    breakdown_steps = 3
+    mih.mih_set_timing(2)
+    kern_ms = {kk: 0.0 for kk in mih.PROF_KINDS}
+    kern_n = {kk: 0 for kk in mih.PROF_KINDS}
+    bstats = {"candidates_raw": 0, "candidates_sliced": 0, "lookups": 0}
+    for _ in range(breakdown_steps):
+        r = step()
+        prof = mih.mih_last_profile()
+        for kk in mih.PROF_KINDS:
+            kern_ms[kk] += prof["kernel_ms"][kk]
+            kern_n[kk] += prof["kernel_launches"][kk]
+        for kk in bstats:
+            bstats[kk] += r["stats"][kk]
+    mih.mih_set_timing(False)
+    torch.cuda.synchronize()
+    kernels = {kk: {"ms_per_step": kern_ms[kk] / breakdown_steps, "launches_per_step": kern_n[kk] / breakdown_steps}
+               for kk in mih.PROF_KINDS if kern_n[kk]}
+
+    # ---- roofline of the dominant kernel, algorithmic bytes
     sparse = [kd == mih.MIH_TABLE_SPARSE for kd in info["table_kind"]]
     bytes_per_lookup = 8 + (8 if all(sparse) else 0)       # bucket bounds (+ one {key, rank} slot)
     # full code per candidate; the id too unless the tables keep codes inline.
@@ -403,23 +428,36 @@ def run_ours(a):
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = (alg_bytes / max(main_launches, 1)) / ((main_ms / max(main_launches, 1)) / 1000.0) / 1e9 \
+    # The whole search (both search kernels, every wave): bytes over the span of
+    # the wave-loop graph in the timed batches (the span also holds each wave's
+    # planning and stopping test, so this rate slightly understates the kernels).
+    span_rate = (alg_bytes / max(main_launches, 1)) / ((main_ms / max(main_launches, 1)) / 1000.0) / 1e9 \
         if main_ms > 0 else None
-    ratio = traffic_ratio() if (q == 128 and kind == "lsh") else None
-    traffic = ratio * alg_bytes / max(main_launches, 1) if ratio else None
-    # main_ms is the span of the wave-loop graph: the fused search kernels plus
-    # each wave's planning and stopping-test kernels (a few % of it), so the
-    # achieved rate is a slight underestimate for the search kernels alone
-    roofline = {"bound": "hbm", "kernel": "search_kernel+search_stream_kernel (fused MIH search, wave-loop graph span)",
+    # The dominant kernel alone: the slice kernel (big buckets), its candidates'
+    # bytes over its own event time in the breakdown batches.
+    slice_ms = kern_ms["slice"] / breakdown_steps
+    slice_launches = kern_n["slice"] / breakdown_steps
+    slice_bytes = (bstats["candidates_sliced"] / breakdown_steps) * bytes_per_cand
+    achieved = slice_bytes / (slice_ms / 1000.0) / 1e9 if slice_ms > 0 else None
+    traffic, traffic_src = slice_traffic(info, slice_launches, bstats, breakdown_steps, q, kind, n, m)
+    roofline = {"bound": "hbm",
+                "kernel": ("search_stream_kernel (big-bucket slices of inline codes or records, streamed by bulk "
+                           "copies)" if info["inline_codes"] else "search_big_kernel (big-bucket slices, by id)"),
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
-                "traffic_source": ("profiles/search_kernels_5e7x128_traffic.txt: dram bytes per algorithmic byte "
-                                   "on the 5e7 case, scaled to this launch") if traffic else None,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "per_launch_ms": main_ms / max(main_launches, 1), "launches_per_step": main_launches / a.steps,
-                "search_share_of_step": main_ms / ms if ms > 0 else None,
-                "alg_bytes_per_step": alg_bytes / a.steps,
-                "bytes_model": f"{bytes_per_lookup} B/lookup + {bytes_per_cand} B/raw candidate"}
+                "traffic_source": traffic_src,
+                "peak_source": "measured (burst copy)" if "hbm_gbs" in peaks else "fallback",
+                "alg_bytes_per_launch": slice_bytes / max(slice_launches, 1e-9),
+                "ms_per_launch": slice_ms / max(slice_launches, 1e-9), "launches_per_step": slice_launches,
+                "bytes_model": f"{bytes_per_cand} B per streamed candidate",
+                "timing": "CUDA events around each launch, host-loop waves, 3 batches after the timed region",
+                "search_span": {"kernels": "search_kernel + slice kernel, every wave (graph span, timed batches)",
+                                "achieved": span_rate, "frac": (span_rate / hbm_peak) if span_rate else None,
+                                "alg_bytes_per_step": alg_bytes / a.steps,
+                                "ms_per_step": main_ms / a.steps,
+                                "bytes_model": f"{bytes_per_lookup} B/lookup + {bytes_per_cand} B/raw candidate",
+                                "share_of_step": main_ms / ms if ms > 0 else None},
+                "kernels_ms_per_step": kernels}
 
     # ---- end to end through the C-ABI with host buffers (pinned), K steps
     qh = queries.cpu().pin_memory()

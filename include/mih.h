@@ -102,7 +102,17 @@ typedef struct {
                               copy of the codes (n * q/8 bytes) and permutes each
                               batch of queries.  mih_greedy_substrings computes
                               the paper's greedy order. */
-    int32_t reserved[8];   /* must be zero */
+    const int32_t *substring_length; /* Per-table substring lengths (the Conclusion,
+                              Sec. 8, leaves them open): NULL = the floor/ceil
+                              layout of Sec. 2.1.  Otherwise a host array of m
+                              lengths, each 1..32, summing to q, read during
+                              mih_build only: table j takes the contiguous bits
+                              [o_j, o_j + length[j]) with o_j the sum of the
+                              lengths before it.  Results are unchanged (Props. 1
+                              and 2 hold for any partition into m disjoint
+                              substrings); only the work per step changes.
+                              mih_cost_layout proposes lengths. */
+    int32_t reserved[6];   /* must be zero */
 } mih_params;
 
 /* mih_params.executor (not part of the paper: a launch strategy). */
@@ -123,6 +133,8 @@ typedef struct {
     uint64_t steps;              /* Alg. 3 steps executed, summed over queries */
     uint64_t phase2_queries;     /* k-NN queries re-collected in a second pass */
     uint64_t waves;              /* search waves launched */
+    uint64_t candidates_sliced;  /* of candidates_raw: entries of big buckets, which the
+                                    slice kernel streams (the rest the chunk kernel reads) */
 } mih_stats;
 
 typedef struct {
@@ -282,7 +294,13 @@ MIH_API mih_status mih_autotune(const uint64_t *codes, uint64_t n, int q, const 
  * one call it returns MIH_ENOMEM (use linscan_knn then).
  * Set-up: the first call on each device looks up the array's device address
  * with cudaGetSymbolAddress (that device current); make this first call on a
- * device before capturing any stream.
+ * device before capturing any stream.  The address is kept for the life of
+ * the process: after cudaDeviceReset on a device, do not call this entry
+ * point on that device again in the same process.
+ * Cost: each query has 4096 first-pass slots (16 times the largest k, 256);
+ * queries whose candidates within the running bound exceed them (many ties
+ * at the k-th distance) are collected by a second scan of the database, so
+ * such calls read the codes twice.
  * Concurrency: all calls on a device share the one array, and each call clears
  * what must start at zero when it begins; calls that overlap on the GPU (from
  * other streams or host threads) race and corrupt each other's results.
@@ -305,6 +323,42 @@ MIH_API mih_status mih_substring_layout(int q, int m, int32_t *offset, int32_t *
  * codes, n codes, substring length s and search radius r:
  * (1 + n / 2^s) (q / s) sum_{z <= floor(s r / q)} C(s, z). */
 MIH_API double mih_cost_model(int q, uint64_t n, int s, int r);
+
+/* Per-table substring lengths for m tables that minimise the cost model of
+ * Eq. 7 (Sec. 3.1) applied table by table to Algorithm 3.  A query that stops
+ * after step t has searched rings 0..floor((t - j) / m) of table j (none when
+ * t < j), and a ring rho of a table of s bits costs C(s, rho) lookups plus
+ * n / 2^s candidates per lookup (uniform codes; Sec. 3 counts a candidate
+ * check as about one lookup).  With weight w[t] on stop step t
+ * (t = 0 .. n_steps - 1, e.g. a histogram of measured stop steps) the cost is
+ *   sum_t w[t] sum_j (1 + n / 2^s_j) sum_{rho <= floor((t - j)/m)} C(s_j, rho),
+ * minimised exactly (dynamic programming over the tables) over lengths
+ * s_j in 1..32 with sum q; among layouts of equal cost the one closest to
+ * q/m per table is taken.  Writes `length` (host, m entries) and returns the
+ * cost, or -1 for invalid arguments (q < 1, m < 1, m > q, q > 32 m,
+ * n_steps < 1, negative weights, NULL pointers). */
+MIH_API double mih_cost_layout(int q, uint64_t n, int m, const double *step_weight, int n_steps,
+                               int32_t *length);
+
+/* ------------------------------------------------------------------------
+ * mih_autotune_layout -- per-table substring lengths for a given m, chosen
+ * by timing on hold-out queries (the selection by validation of Sec. 6,
+ * applied to the lengths the Conclusion leaves open).  Runs the hold-out
+ * queries once on the Sec. 2.1 layout with per-query counters to measure
+ * their stop steps, proposes mih_cost_layout's lengths for that histogram,
+ * then times one mih_knn of each layout (after an untimed one) and writes
+ * the faster layout's lengths.
+ * codes, n, q, queries, nq, k, params  as in mih_autotune (params must not
+ *               set substring_length).
+ * m            number of tables (substrings of at most 32 bits).
+ * best_length  host out, m entries.
+ * ms_per_query host out, nullable, double[2]: the Sec. 2.1 layout, the
+ *              cost-model layout (the same figure when both are equal).
+ * Synchronises `stream`.  Errors as mih_autotune.
+ */
+MIH_API mih_status mih_autotune_layout(const uint64_t *codes, uint64_t n, int q, const uint64_t *queries,
+                                       uint32_t nq, uint32_t k, int m, const mih_params *params, void *stream,
+                                       int32_t *best_length, double *ms_per_query);
 
 /* Number of substrings suggested by Sec. 3.1 / Table 4: the integer closest
  * to q / log2(n), clamped so that no substring exceeds 32 bits and m <= q. */
@@ -342,20 +396,52 @@ MIH_API mih_status mih_bit_correlation(const uint64_t *codes, uint64_t n, int q,
  * Per-call profile of the calling host thread (not part of the paper).
  * With timing enabled, mih_knn, mih_rnear and linscan_knn record CUDA events
  * on their stream around their main kernels (the fused search kernels, the
- * linear-scan kernel) and around the whole call.
+ * linear-scan kernel) and around the whole call.  With per-kernel timing
+ * (level 2) they also record an event pair around every launch of the kinds
+ * below, and mih_knn runs its waves from a host loop (MIH_EXEC_HOST: the
+ * same kernels and results, but each launch can be bracketed by events).
  */
+enum {
+    MIH_PROF_CHUNK = 0,     /* search_kernel: ring chunks (lookups, small buckets) */
+    MIH_PROF_SLICE = 1,     /* search_stream_kernel / search_big_kernel: big-bucket slices */
+    MIH_PROF_PROBE = 2,     /* bound_probe_kernel */
+    MIH_PROF_PLAN = 3,      /* per-wave chunk planning (counts and their scan) */
+    MIH_PROF_STOP = 4,      /* knn_stop_kernel: the stopping test of Alg. 3 */
+    MIH_PROF_SELECT = 5,    /* select_kernel */
+    MIH_PROF_RESOLVE = 6,   /* resolve_ids_kernel */
+    MIH_PROF_SCAN = 7,      /* linscan_kernel */
+    MIH_PROF_KINDS = 8
+};
+
 typedef struct {
     uint64_t launches;       /* kernel launches issued by the last call */
     uint64_t main_launches;  /* launches of the main kernels */
     double main_ms;          /* summed device time of the main kernels (timing on) */
     double call_ms;          /* device time from first to last launch (timing on) */
+    double kernel_ms[MIH_PROF_KINDS];         /* per kind, summed (timing level 2) */
+    uint64_t kernel_launches[MIH_PROF_KINDS]; /* per kind, launches timed (level 2) */
 } mih_profile;
 
-/* Enable (1) or disable (0) event timing for calls from this host thread. */
-MIH_API void mih_set_timing(int enable);
+/* Timing for calls from this host thread: 0 off, 1 main kernels and the
+ * call, 2 also every kernel kind above (and host-loop waves in mih_knn). */
+MIH_API void mih_set_timing(int level);
 
 /* Profile of this thread's last mih_knn / mih_rnear / linscan_knn call. */
 MIH_API mih_status mih_last_profile(mih_profile *out);
+
+/* ------------------------------------------------------------------------
+ * mih_set_wait_limit -- bounded device waits (not part of the paper).
+ * The slice kernel of mih_knn / mih_rnear waits on its bulk copies into
+ * shared memory; a wait that runs past `limit_us` microseconds (0 = the
+ * default of one second) gives up, the kernel drains the copies it still has
+ * in flight (each with the one-second limit) and the call returns
+ * MIH_ETIMEOUT.  expire_first_wait = 1 is for testing that path: the first
+ * wait of each warp of the slice kernel is made on a barrier that no copy
+ * completes, so every call that streams a big bucket returns MIH_ETIMEOUT
+ * after about `limit_us`; 0 restores normal waits.  Applies to calls from the
+ * calling host thread.  Errors: MIH_EINVAL when limit_us exceeds 60 s.
+ */
+MIH_API mih_status mih_set_wait_limit(uint32_t limit_us, int expire_first_wait);
 
 /* Static text of a status code. */
 MIH_API const char *mih_status_str(mih_status s);

@@ -32,7 +32,8 @@ EXPORTS = (
     "mih_build", "mih_free", "mih_index_get_info", "mih_knn", "mih_rnear", "linscan_knn",
     "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
-    "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation",
+    "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation", "mih_set_wait_limit",
+    "mih_cost_layout", "mih_autotune_layout",
 )
 
 
@@ -46,23 +47,34 @@ class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
                 ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("executor", ctypes.c_int32),
                 ("pad_", ctypes.c_int32), ("bit_order", ctypes.POINTER(ctypes.c_int32)),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("substring_length", ctypes.POINTER(ctypes.c_int32)), ("reserved", ctypes.c_int32 * 6)]
 
 
 class mih_stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in (
-        "lookups", "candidates_raw", "candidates_unique", "steps", "phase2_queries", "waves")]
+        "lookups", "candidates_raw", "candidates_unique", "steps", "phase2_queries", "waves",
+        "candidates_sliced")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
+# mih_profile.kernel_ms / kernel_launches index (MIH_PROF_* in include/mih.h)
+PROF_KINDS = ("chunk", "slice", "probe", "plan", "stop", "select", "resolve", "scan")
+
+
 class mih_profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("main_launches", ctypes.c_uint64),
-                ("main_ms", ctypes.c_double), ("call_ms", ctypes.c_double)]
+                ("main_ms", ctypes.c_double), ("call_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double * len(PROF_KINDS)),
+                ("kernel_launches", ctypes.c_uint64 * len(PROF_KINDS))]
 
     def as_dict(self):
-        return {f: (float(getattr(self, f)) if "ms" in f else int(getattr(self, f))) for f, _ in self._fields_}
+        d = {f: (float(getattr(self, f)) if "ms" in f else int(getattr(self, f)))
+             for f in ("launches", "main_launches", "main_ms", "call_ms")}
+        d["kernel_ms"] = {k: float(v) for k, v in zip(PROF_KINDS, self.kernel_ms)}
+        d["kernel_launches"] = {k: int(v) for k, v in zip(PROF_KINDS, self.kernel_launches)}
+        return d
 
 
 class mih_index_info(ctypes.Structure):
@@ -105,6 +117,10 @@ def load():
     lib.mih_substring_layout.restype = st
     lib.mih_cost_model.argtypes = [i32, u64, i32, i32]
     lib.mih_cost_model.restype = ctypes.c_double
+    lib.mih_cost_layout.argtypes = [i32, u64, i32, P, i32, P]
+    lib.mih_cost_layout.restype = ctypes.c_double
+    lib.mih_autotune_layout.argtypes = [P, u64, i32, P, u32, u32, i32, P, P, P, P]
+    lib.mih_autotune_layout.restype = st
     lib.mih_suggest_m.argtypes = [i32, u64]
     lib.mih_suggest_m.restype = i32
     lib.mih_status_str.argtypes = [st]
@@ -117,6 +133,8 @@ def load():
     lib.mih_autotune.restype = st
     lib.linscan_knn_noalloc.argtypes = [P, u64, i32, P, u32, u32, P, P, P]
     lib.linscan_knn_noalloc.restype = st
+    lib.mih_set_wait_limit.argtypes = [u32, i32]
+    lib.mih_set_wait_limit.restype = st
     lib.mih_set_timing.argtypes = [i32]
     lib.mih_set_timing.restype = None
     lib.mih_last_profile.argtypes = [P]
@@ -174,8 +192,16 @@ def mih_version() -> str:
     return load().mih_version().decode()
 
 
-def mih_set_timing(enable: bool):
-    load().mih_set_timing(1 if enable else 0)
+def mih_set_timing(level):
+    """0/False off, 1/True main kernels and the call, 2 also every kernel kind
+    (mih_knn then runs its waves from a host loop)."""
+    load().mih_set_timing(int(level))
+
+
+def mih_set_wait_limit(limit_us: int = 0, expire_first_wait: bool = False):
+    """Limit of the bounded device waits of this thread's calls (0 = 1 s); with
+    expire_first_wait the slice kernel's first waits run out (timeout test)."""
+    _check(load().mih_set_wait_limit(limit_us, 1 if expire_first_wait else 0), "mih_set_wait_limit")
 
 
 def mih_last_profile() -> dict:
@@ -197,6 +223,17 @@ def mih_cost_model(q: int, n: int, s: int, r: int) -> float:
 
 def mih_suggest_m(q: int, n: int) -> int:
     return int(load().mih_suggest_m(q, n))
+
+
+def mih_cost_layout(q: int, n: int, m: int, step_weight):
+    """Per-table lengths minimising Eq. 7 table by table over Alg. 3 stopped at
+    step t with weight step_weight[t].  Returns (lengths list, cost)."""
+    w = np.ascontiguousarray(step_weight, dtype=np.float64)
+    out = np.zeros(max(m, 1), dtype=np.int32)
+    c = float(load().mih_cost_layout(q, n, m, w.ctypes.data, int(w.size), out.ctypes.data))
+    if c < 0:
+        raise MihError(MIH_EINVAL, "mih_cost_layout", "invalid arguments")
+    return [int(x) for x in out[:m]], c
 
 
 def mih_greedy_substrings(corr, m: int, seed: int = 0):
@@ -262,7 +299,7 @@ class MihIndex:
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
               inline_codes: int = 0, probe: int = 0, executor: int = MIH_EXEC_AUTO, bit_order=None,
-              stream=None) -> MihIndex:
+              substring_length=None, stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
@@ -275,6 +312,9 @@ def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_fact
         if order.shape != (q,):
             raise ValueError("bit_order must hold q entries")
         p.bit_order = order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    if substring_length is not None:
+        lens = np.ascontiguousarray(substring_length, dtype=np.int32)
+        p.substring_length = lens.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     h = ctypes.c_void_p()
     _check(load().mih_build(ptr, n, q, m, ctypes.byref(p), _stream(stream), ctypes.byref(h)), "mih_build")
     return MihIndex(h, codes, q, m)
@@ -295,6 +335,21 @@ def mih_autotune(codes, q: int, queries, k: int, candidates=None, stream=None, *
                                _stream(stream), ctypes.byref(best), times), "mih_autotune")
     ms = list(candidates) if candidates else [mih_suggest_m(q, n) + d for d in (-1, 0, 1)]
     return best.value, {m: t for m, t in zip(ms, times) if t >= 0}
+
+
+def mih_autotune_layout(codes, q: int, queries, k: int, m: int, stream=None, **build):
+    """Per-table lengths for m tables, timed on hold-out queries.  Returns
+    (lengths, {"uniform": ms per query, "cost_model": ms per query})."""
+    cptr, n = _codes_arg(codes, q)
+    qptr, nq = _codes_arg(queries, q)
+    p = mih_params()
+    for key, v in build.items():
+        setattr(p, key, v)
+    out = np.zeros(m, dtype=np.int32)
+    times = (ctypes.c_double * 2)()
+    _check(load().mih_autotune_layout(cptr, n, q, qptr, nq, k, m, ctypes.byref(p), _stream(stream),
+                                      out.ctypes.data, times), "mih_autotune_layout")
+    return [int(x) for x in out], {"uniform": times[0], "cost_model": times[1]}
 
 
 def mih_free(index: MihIndex):

@@ -27,29 +27,68 @@ void clear_error() { g_err[0] = '\0'; }
 // ---------------------------------------------------------------- profile
 namespace {
 struct Profiler {
-    bool timing = false;
+    int timing = 0;                   // 0 off, 1 main spans, 2 also per-kernel spans
     int depth = 0;
-    mih_profile last = {0, 0, 0.0, 0.0};
-    mih_profile cur = {0, 0, 0.0, 0.0};
+    mih_profile last = {};
+    mih_profile cur = {};
     std::vector<cudaEvent_t> events;  // pool; pairs [2i, 2i+1] are main-kernel spans
     size_t used = 0;
+    std::vector<cudaEvent_t> kevents; // pool; pairs [2i, 2i+1] are kernel spans of kind kkind[i]
+    size_t kused = 0;
+    std::vector<int> kkind;
     cudaEvent_t call_start = nullptr, call_stop = nullptr;
 };
 thread_local Profiler g_prof;
 
-cudaEvent_t next_event() {
-    Profiler& p = g_prof;
-    if (p.used == p.events.size()) {
+cudaEvent_t pooled_event(std::vector<cudaEvent_t>& pool, size_t& used) {
+    if (used == pool.size()) {
         cudaEvent_t e = nullptr;
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        p.events.push_back(e);
+        pool.push_back(e);
     }
-    return p.events[p.used++];
+    return pool[used++];
 }
+
+cudaEvent_t next_event() { return pooled_event(g_prof.events, g_prof.used); }
 }  // namespace
+
+int timing_level() { return g_prof.timing; }
+
+KernelSpan::KernelSpan(cudaStream_t s, int kind, bool active) : s_(s), on_(false) {
+    Profiler& p = g_prof;
+    if (!active || p.timing < 2 || p.depth == 0 || kind < 0 || kind >= MIH_PROF_KINDS) return;
+    cudaEvent_t e = pooled_event(p.kevents, p.kused);
+    if (!e) return;
+    if (cudaEventRecord(e, s) != cudaSuccess) {
+        cudaGetLastError();
+        --p.kused;
+        return;
+    }
+    p.kkind.push_back(kind);
+    on_ = true;
+}
+
+KernelSpan::~KernelSpan() {
+    if (!on_) return;
+    Profiler& p = g_prof;
+    cudaEvent_t e = pooled_event(p.kevents, p.kused);
+    if (e && cudaEventRecord(e, s_) == cudaSuccess) return;
+    cudaGetLastError();
+    // drop this span: its end event (if taken) and its begin event
+    if (e) --p.kused;
+    --p.kused;
+    p.kkind.pop_back();
+}
+
+// Limit of the bounded waits on bulk copies, and the timeout test switch
+// (mih_set_wait_limit), per host thread.
+thread_local uint64_t g_wait_ns = 1000000000ull;
+thread_local bool g_wait_test = false;
+uint64_t wait_limit_ns() { return g_wait_ns; }
+bool wait_test_expire() { return g_wait_test; }
 
 void note_launch() { g_prof.cur.launches++; }
 uint64_t launches_so_far() { return g_prof.cur.launches; }
@@ -76,8 +115,10 @@ void main_kernel_end(cudaStream_t s) {
 CallScope::CallScope(cudaStream_t s) : s_(s) {
     Profiler& p = g_prof;
     if (p.depth++ > 0) return;
-    p.cur = {0, 0, 0.0, 0.0};
+    p.cur = mih_profile{};
     p.used = 0;
+    p.kused = 0;
+    p.kkind.clear();
     if (p.timing) {
         if (!p.call_start) cudaEventCreate(&p.call_start);
         if (!p.call_stop) cudaEventCreate(&p.call_stop);
@@ -99,6 +140,14 @@ CallScope::~CallScope() {
                 if (cudaEventElapsedTime(&m, p.events[i], p.events[i + 1]) == cudaSuccess) main_ms += m;
             }
             p.cur.main_ms = main_ms;
+            for (size_t i = 0; i + 1 < p.kused && i / 2 < p.kkind.size(); i += 2) {
+                const int kind = p.kkind[i / 2];
+                float m = 0.f;
+                if (kind >= 0 && cudaEventElapsedTime(&m, p.kevents[i], p.kevents[i + 1]) == cudaSuccess) {
+                    p.cur.kernel_ms[kind] += m;
+                    p.cur.kernel_launches[kind] += 1;
+                }
+            }
         }
         cudaGetLastError();
     }
@@ -256,7 +305,17 @@ const char* mih_status_str(mih_status s) {
 
 const char* mih_last_error(void) { return mih::g_err; }
 
-void mih_set_timing(int enable) { mih::g_prof.timing = enable != 0; }
+void mih_set_timing(int level) { mih::g_prof.timing = level < 0 ? 0 : (level > 2 ? 2 : level); }
+
+mih_status mih_set_wait_limit(uint32_t limit_us, int expire_first_wait) {
+    if (limit_us > 60u * 1000u * 1000u) {
+        mih::set_error("mih_set_wait_limit: limit above one minute (%u us)", limit_us);
+        return MIH_EINVAL;
+    }
+    mih::g_wait_ns = limit_us == 0 ? 1000000000ull : 1000ull * limit_us;
+    mih::g_wait_test = expire_first_wait != 0;
+    return MIH_OK;
+}
 
 mih_status mih_last_profile(mih_profile* out) {
     if (!out) {
@@ -296,6 +355,67 @@ double mih_cost_model(int q, uint64_t n, int s, int r) {
         c = c * (s - z) / (z + 1);
     }
     return (1.0 + static_cast<double>(n) / ldexp(1.0, s)) * (static_cast<double>(q) / s) * ball;
+}
+
+// Eq. 7 table by table over Algorithm 3's schedule (see include/mih.h): the
+// cost of table j with s bits, weighted over the stop steps, is
+// (1 + n / 2^s) sum_t w[t] sum_{rho <= floor((t - j)/m)} C(s, rho); the layout
+// is the exact minimum of the sum over tables with sum_j s_j = q, by dynamic
+// programming over (tables done, bits used).
+double mih_cost_layout(int q, uint64_t n, int m, const double* w, int n_steps, int32_t* length) {
+    if (q < 1 || m < 1 || m > q || q > 32 * m || n_steps < 1 || !w || !length) return -1.0;
+    for (int t = 0; t < n_steps; ++t)
+        if (!(w[t] >= 0.0)) return -1.0;
+    // C(s, rho) for s <= 32
+    double C[33][33] = {};
+    for (int a = 0; a <= 32; ++a) {
+        C[a][0] = 1.0;
+        for (int b = 1; b <= a; ++b) C[a][b] = C[a - 1][b - 1] + (b <= a - 1 ? C[a - 1][b] : 0.0);
+    }
+    // table cost cost[j][s]
+    std::vector<double> cost(static_cast<size_t>(m) * 33, 0.0);
+    for (int j = 0; j < m; ++j)
+        for (int sb = 1; sb <= 32; ++sb) {
+            double rings = 0.0;
+            for (int t = j; t < n_steps; ++t) {
+                if (w[t] == 0.0) continue;
+                const int rmax = (t - j) / m;
+                double ball = 0.0;
+                for (int r = 0; r <= rmax && r <= sb; ++r) ball += C[sb][r];
+                rings += w[t] * ball;
+            }
+            cost[static_cast<size_t>(j) * 33 + sb] = (1.0 + static_cast<double>(n) / ldexp(1.0, sb)) * rings;
+        }
+    // best[j][b]: (cost, squared deviation from q/m) of tables 0..j-1 on b bits
+    const double inf = HUGE_VAL, mean = static_cast<double>(q) / m;
+    std::vector<double> bc(static_cast<size_t>(m + 1) * (q + 1), inf), bd = bc;
+    std::vector<int> pick(static_cast<size_t>(m + 1) * (q + 1), 0);
+    auto at = [q](int j, int b) { return static_cast<size_t>(j) * (q + 1) + b; };
+    bc[at(0, 0)] = 0.0;
+    bd[at(0, 0)] = 0.0;
+    for (int j = 0; j < m; ++j)
+        for (int b = 0; b <= q; ++b) {
+            if (bc[at(j, b)] == inf) continue;
+            for (int sb = 1; sb <= 32 && b + sb <= q; ++sb) {
+                const double c = bc[at(j, b)] + cost[static_cast<size_t>(j) * 33 + sb];
+                const double d = bd[at(j, b)] + (sb - mean) * (sb - mean);
+                double& oc = bc[at(j + 1, b + sb)];
+                double& od = bd[at(j + 1, b + sb)];
+                const double tol = 1e-12 * (c > oc ? c : oc);
+                const bool better = oc == inf || c < oc - tol || (c <= oc + tol && d < od);
+                if (better) {
+                    oc = c;
+                    od = d;
+                    pick[at(j + 1, b + sb)] = sb;
+                }
+            }
+        }
+    if (bc[at(m, q)] == inf) return -1.0;
+    for (int j = m, b = q; j > 0; --j) {
+        length[j - 1] = pick[at(j, b)];
+        b -= length[j - 1];
+    }
+    return bc[at(m, q)];
 }
 
 // Sec. 3.1 / Table 4: m close to q / log2(n); no substring above 32 bits.

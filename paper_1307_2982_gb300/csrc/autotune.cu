@@ -1,7 +1,9 @@
 // autotune.cu -- choose m by timing the search on hold-out queries (Sec. 6
-// "Number of Substrings").  Host code over the library's own entry points.
+// "Number of Substrings"), and per-table substring lengths for a given m the
+// same way.  Host code over the library's own entry points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "launch.h"
@@ -18,6 +20,10 @@ extern "C" mih_status mih_autotune(const uint64_t* codes, uint64_t n, int q, con
     *best_m = 0;
     if (nq == 0 || k == 0 || k > MIH_MAX_K) {
         set_error("mih_autotune: need at least one hold-out query and 1 <= k <= %u", MIH_MAX_K);
+        return MIH_EINVAL;
+    }
+    if (params && params->substring_length) {
+        set_error("mih_autotune: params.substring_length must be NULL (lengths depend on m)");
         return MIH_EINVAL;
     }
     std::vector<int> cand;
@@ -81,4 +87,113 @@ extern "C" mih_status mih_autotune(const uint64_t* codes, uint64_t n, int q, con
         return MIH_EINVAL;
     }
     return st;
+}
+
+// Per-table lengths for a given m: the stop steps of the hold-out queries on
+// the Sec. 2.1 layout (per-query counters), mih_cost_layout's lengths for
+// their histogram, then one timed mih_knn of each layout.
+extern "C" mih_status mih_autotune_layout(const uint64_t* codes, uint64_t n, int q, const uint64_t* queries,
+                                          uint32_t nq, uint32_t k, int m, const mih_params* params, void* stream,
+                                          int32_t* best_length, double* ms_per_query) {
+    using namespace mih;
+    clear_error();
+    if (!best_length) {
+        set_error("mih_autotune_layout: best_length is NULL");
+        return MIH_EINVAL;
+    }
+    if (nq == 0 || k == 0 || k > MIH_MAX_K) {
+        set_error("mih_autotune_layout: need at least one hold-out query and 1 <= k <= %u", MIH_MAX_K);
+        return MIH_EINVAL;
+    }
+    if (m < 1 || m > q || (q + m - 1) / m > 32) {
+        set_error("mih_autotune_layout: need 1 <= m <= q and substrings of at most 32 bits (q=%d m=%d)", q, m);
+        return MIH_EINVAL;
+    }
+    if (params && params->substring_length) {
+        set_error("mih_autotune_layout: params.substring_length must be NULL (the call chooses it)");
+        return MIH_EINVAL;
+    }
+    if (ms_per_query) ms_per_query[0] = ms_per_query[1] = -1.0;
+    mih_params base = {};
+    if (params) base = *params;
+    std::vector<int32_t> uni_off(m), uni_len(m);
+    MIH_TRY(mih_substring_layout(q, m, uni_off.data(), uni_len.data()));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* ids = nullptr;
+    int32_t* dist = nullptr;
+    uint64_t* qstats = nullptr;
+    MIH_CUDA(cudaMalloc(&ids, sizeof(uint32_t) * nq * static_cast<size_t>(k)));
+    if (cudaMalloc(&dist, sizeof(int32_t) * nq * static_cast<size_t>(k)) != cudaSuccess ||
+        cudaMalloc(&qstats, sizeof(uint64_t) * 4 * static_cast<size_t>(nq)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ids);
+        cudaFree(dist);
+        set_error("mih_autotune_layout: output allocation failed");
+        return MIH_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // time one layout: untimed call, timed call; ms per query
+    auto time_layout = [&](const int32_t* len, double* per_q, bool stop_steps, std::vector<double>* hist) {
+        mih_params p = base;
+        p.substring_length = len;
+        mih_index* ix = nullptr;
+        mih_status st = mih_build(codes, n, q, m, &p, stream, &ix);
+        if (st != MIH_OK) return st;
+        if (stop_steps) {
+            st = mih_knn(ix, queries, nq, nullptr, k, nullptr, ids, dist, qstats, nullptr, stream);
+            if (st == MIH_OK) {
+                std::vector<uint64_t> h(4ull * nq);
+                if (cudaMemcpy(h.data(), qstats, sizeof(uint64_t) * 4 * nq, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    cudaGetLastError();
+                    set_error("mih_autotune_layout: counter copy failed");
+                    st = MIH_ECUDA;
+                } else {
+                    hist->assign(static_cast<size_t>(q) + 1, 0.0);
+                    for (uint32_t i = 0; i < nq; ++i) (*hist)[std::min<uint64_t>(h[4ull * i + 3], q)] += 1.0;
+                }
+            }
+        }
+        if (st == MIH_OK) st = mih_knn(ix, queries, nq, nullptr, k, nullptr, ids, dist, nullptr, nullptr, stream);
+        if (st == MIH_OK) {
+            cudaEventRecord(e0, s);
+            st = mih_knn(ix, queries, nq, nullptr, k, nullptr, ids, dist, nullptr, nullptr, stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            *per_q = ms / nq;
+        }
+        mih_free(ix);
+        return st;
+    };
+    double t_uni = -1.0, t_cost = -1.0;
+    std::vector<double> hist;
+    std::vector<int32_t> cost_len(m);
+    mih_status st = time_layout(uni_len.data(), &t_uni, n > 0, &hist);
+    bool same = true;
+    if (st == MIH_OK && n > 0) {
+        if (mih_cost_layout(q, n, m, hist.data(), static_cast<int>(hist.size()), cost_len.data()) < 0) {
+            set_error("mih_autotune_layout: cost model failed");
+            st = MIH_EINTERNAL;
+        } else {
+            for (int j = 0; j < m; ++j) same = same && cost_len[j] == uni_len[j];
+            if (!same) st = time_layout(cost_len.data(), &t_cost, false, nullptr);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ids);
+    cudaFree(dist);
+    cudaFree(qstats);
+    if (st != MIH_OK) return st;
+    if (same) t_cost = t_uni;
+    if (ms_per_query) {
+        ms_per_query[0] = t_uni;
+        ms_per_query[1] = t_cost;
+    }
+    const int32_t* best = (!same && t_cost < t_uni) ? cost_len.data() : uni_len.data();
+    for (int j = 0; j < m; ++j) best_length[j] = best[j];
+    return MIH_OK;
 }

@@ -329,9 +329,25 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
         set_error("mih_build: q must be 64, 128 or 256 (got %d)", q);
         return MIH_EINVAL;
     }
-    if (m < 1 || m > q || (q + m - 1) / m > 32) {
-        set_error("mih_build: need 1 <= m <= q and substrings of at most 32 bits (q=%d m=%d)", q, m);
+    const int32_t* lengths = params ? params->substring_length : nullptr;
+    if (m < 1 || m > q || m > kMaxTables || (!lengths && (q + m - 1) / m > 32)) {
+        set_error("mih_build: need 1 <= m <= min(q, %d) and substrings of at most 32 bits (q=%d m=%d)", kMaxTables,
+                  q, m);
         return MIH_EINVAL;
+    }
+    if (lengths) {
+        int sum = 0;
+        for (int j = 0; j < m; ++j) {
+            if (lengths[j] < 1 || lengths[j] > 32) {
+                set_error("mih_build: substring_length[%d] = %d is outside 1..32", j, lengths[j]);
+                return MIH_EINVAL;
+            }
+            sum += lengths[j];
+        }
+        if (sum != q) {
+            set_error("mih_build: substring lengths sum to %d, not q = %d", sum, q);
+            return MIH_EINVAL;
+        }
     }
     if (n >= 0xFFFFFFFFull) {
         set_error("mih_build: n must be below 2^32 - 1 (ids are uint32)");
@@ -339,7 +355,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     }
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 6; ++i)
             if (params->reserved[i] != 0 || params->pad_ != 0) {
                 set_error("mih_build: params.reserved and params.pad_ must be zero");
                 return MIH_EINVAL;
@@ -424,7 +440,14 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->distinct_keys.assign(m, 0);
     ix->max_bucket.assign(m, 0);
     int32_t off[kMaxTables], len[kMaxTables];
-    mih_substring_layout(q, m, off, len);
+    if (lengths) {
+        for (int j = 0, o = 0; j < m; o += lengths[j], ++j) {
+            off[j] = o;
+            len[j] = lengths[j];
+        }
+    } else {
+        mih_substring_layout(q, m, off, len);
+    }
     mih_status st = MIH_OK;
     for (int j = 0; j < m && st == MIH_OK; ++j) {
         memset(&ix->tables[j], 0, sizeof(TableDesc));

@@ -23,6 +23,28 @@ uint64_t launches_so_far();                                  // launches counted
 void add_launches(uint64_t launches, uint64_t main_launches);  // work a graph repeated on the device
 void main_kernel_begin(cudaStream_t s);
 void main_kernel_end(cudaStream_t s);
+// Bounded device waits of the calling host thread (mih_set_wait_limit): the
+// limit in ns (default one second) and the timeout test switch.
+uint64_t wait_limit_ns();
+bool wait_test_expire();
+// Timing level of the calling thread (mih_set_timing).
+int timing_level();
+
+// An event pair around one kernel launch of the given MIH_PROF_* kind, on
+// stream s, recorded only with per-kernel timing (level 2) inside a C-ABI
+// call and when `active` (false while the stream is being captured).
+class KernelSpan {
+   public:
+    KernelSpan(cudaStream_t s, int kind, bool active = true);
+    ~KernelSpan();
+    KernelSpan(const KernelSpan&) = delete;
+    KernelSpan& operator=(const KernelSpan&) = delete;
+
+   private:
+    cudaStream_t s_;
+    bool on_;
+};
+
 class CallScope {
    public:
     explicit CallScope(cudaStream_t s);

@@ -400,7 +400,10 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         a.cnt = cnt;
         const dim3 grid(qtiles, static_cast<unsigned>(splits));
         main_kernel_begin(s);
-        MIH_TRY(launch_scan(a, W, G, grid, s));
+        {
+            KernelSpan ks(s, MIH_PROF_SCAN);
+            MIH_TRY(launch_scan(a, W, G, grid, s));
+        }
         main_kernel_end(s);
 
         finish_first_pass_kernel<<<grid1(nq + 1), 256, 0, s>>>(nq, q, n, k, k_uniform, hist, cnt, cap, dk, thr, need,
@@ -473,7 +476,8 @@ namespace {
 
 constexpr uint32_t kNaMaxQueries = 256;        // queries per call
 constexpr uint32_t kNaMaxK = 256;              // k per call
-constexpr uint32_t kNaCap = 4096;              // first-pass slots per query
+constexpr uint32_t kNaCap = 16 * kNaMaxK;      // first-pass slots per query (4096); a query that
+                                               // keeps more is collected by a second scan
 constexpr uint64_t kNaSecond = 1ull << 20;     // second-pass slots per call
 
 constexpr size_t na_align(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }

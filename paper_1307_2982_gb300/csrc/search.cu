@@ -47,10 +47,13 @@ constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;   // one shared-memory stage o
 
 // Entries per stage of the slice kernel: whole codes (W uint64 words), or
 // records of 2W - 1 uint32 words (inline records, every substring one 32-bit
-// word), rounded down to whole warp rows.
+// word).  A stage of records is read in groups of four records (16 (2W - 1)
+// bytes, 16-byte aligned) that start at a multiple of four, and its copy
+// starts up to three records early: it holds the whole groups that fit in
+// kStageBytes, less those three records.
 template <int W, bool REDUCED>
 __host__ __device__ constexpr uint32_t stage_entries() {
-    return REDUCED ? ((kStageBytes / (4 * (2 * W - 1))) & ~31u) : kStageBytes / (8 * W);
+    return REDUCED ? 4u * (kStageBytes / (16u * (2 * W - 1))) - 3u : kStageBytes / (8 * W);
 }
 
 // Entries per big-bucket slice: 1024 whole codes, or four full stages of
@@ -100,6 +103,9 @@ struct SearchArgs {
     int inline_codes;                  // tables keep codes in bucket order
     int* timeout;                      // set when a bounded wait gives up
     int exact_stats;                   // count every unique candidate (per-query counters requested)
+    uint64_t wait_ns;                  // limit of a bounded wait on stage data
+    int wait_test;                     // timeout test: each warp's first wait runs out
+    unsigned long long* sliced;        // raw candidates queued as big-bucket slices (nullable)
 };
 
 // Chunks of step t for a query: ceil(C(s_j, rho) / 256), 0 if rho > s_j.
@@ -622,7 +628,7 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
             fits = static_cast<uint64_t>(base) + ns_total <= a.big_cap;
         }
         int nz = 0;
-        uint32_t tot = 0;
+        uint32_t tot = 0, sliced = 0;
 #pragma unroll
         for (int r = 0; r < kKeysPerLane; ++r) {
             uint32_t sz = ee[r] - bb[r];
@@ -639,6 +645,7 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
                 }
                 if (fits) {
                     raw += sz;
+                    sliced += sz;
                     sz = 0;
                 }
             }
@@ -679,6 +686,34 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
                     valid[k] = idx < total;
                     pos[k] = valid[k] ? ent.x + (idx - ent.y) : 0u;
                 }
+                if constexpr (ALIGNED) {
+                    if (tab.rec_words != 0) {
+                        // inline records of this table: R consecutive words at
+                        // each position, read in place (no id, no gather)
+                        constexpr int R = 2 * W - 1;
+                        const uint32_t* recs = reinterpret_cast<const uint32_t*>(tab.codes);
+                        uint32_t g32[2 * W], gq[R], th[R];
+#pragma unroll
+                        for (int w = 0; w < W; ++w) {
+                            g32[2 * w] = static_cast<uint32_t>(g.w[w]);
+                            g32[2 * w + 1] = static_cast<uint32_t>(g.w[w] >> 32);
+                        }
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            gq[i] = i < j ? g32[i] : g32[i + 1];
+                            th[i] = static_cast<uint32_t>(rho) + (i < j ? 1u : 0u);
+                        }
+                        uint32_t rec[kBatch][R];
+#pragma unroll
+                        for (int k = 0; k < kBatch; ++k)
+#pragma unroll
+                            for (int i = 0; i < R; ++i)
+                                rec[k][i] = valid[k] ? __ldg(recs + static_cast<uint64_t>(pos[k]) * R + i) : 0u;
+                        process_records<R, MODE, kBatch>(a, whist, q, j, rho, bnd, a.m * rho + j > hd, gq, th,
+                                                         tab.ids, pos, valid, rec, unique);
+                        continue;
+                    }
+                }
                 uint32_t unused = 0;
                 handle_batch<W, MODE, ALIGNED, kBatch>(a, L, whist, q, j, rho, -1, hd, bnd, g, src, pos, valid,
                                                        unique, unused);
@@ -690,7 +725,11 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
         // steps not counted before
         const bool counting = t > hd;
         uint32_t lk = counting ? static_cast<uint32_t>(mine) : 0u;
-        if (!counting) raw = 0;
+        if (!counting) raw = sliced = 0;
+        if (a.sliced) {
+            const uint32_t ws = __reduce_add_sync(0xFFFFFFFFu, sliced);
+            if (lane == 0 && ws != 0) atomicAdd(a.sliced, static_cast<unsigned long long>(ws));
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             lk += __shfl_down_sync(0xFFFFFFFFu, lk, o);
@@ -832,6 +871,34 @@ constexpr uint32_t kWaitHintNs = 20000;          // longest suspension of one tr
 constexpr uint64_t kWaitNs = 1000000000ull;      // a bulk copy not done after 1 s is an error
 constexpr uint32_t kStageSlot = kStageBytes + 16;   // + one 8-byte code of realignment (W = 1)
 
+// Largest bulk copy issue_stage makes for one stage: records start up to three
+// entries early (16-byte aligned groups of four), W = 1 codes up to one, and
+// both round the size up to 16 bytes.  Every layout must fit its slot.
+template <int W, bool REDUCED>
+constexpr uint32_t max_stage_copy() {
+    return REDUCED ? (((stage_entries<W, true>() + 3u) * 4u * (2 * W - 1) + 15u) & ~15u)
+                   : (W == 1 ? (((stage_entries<1, false>() + 1u) * 8u + 15u) & ~15u)
+                             : stage_entries<W, false>() * 8u * W);
+}
+static_assert(max_stage_copy<1, false>() <= kStageSlot && max_stage_copy<2, false>() <= kStageSlot &&
+                  max_stage_copy<4, false>() <= kStageSlot,
+              "a stage of whole codes overruns its shared-memory slot");
+static_assert(max_stage_copy<1, true>() <= kStageSlot && max_stage_copy<2, true>() <= kStageSlot &&
+                  max_stage_copy<4, true>() <= kStageSlot,
+              "a stage of records overruns its shared-memory slot");
+static_assert(stage_entries<1, true>() >= 32 && stage_entries<2, true>() >= 32 && stage_entries<4, true>() >= 32 &&
+                  stage_entries<4, false>() % 32 == 0,
+              "a stage holds at least a warp row of entries");
+// Groups of four records read by one lane (16-byte shared loads), and the
+// groups a stage can span; every group a lane reads lies inside its slot.
+template <int W>
+constexpr uint32_t stage_groups() {
+    return (3u + stage_entries<W, true>() + 3u) / 4u;
+}
+static_assert(stage_groups<1>() * 16u * (2 * 1 - 1) <= kStageSlot && stage_groups<2>() * 16u * (2 * 2 - 1) <= kStageSlot &&
+                  stage_groups<4>() * 16u * (2 * 4 - 1) <= kStageSlot,
+              "record groups of a stage overrun its shared-memory slot");
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -858,22 +925,26 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Waits for the phase of `bar` with the given parity.  Each try_wait may
 // suspend the warp (up to kWaitHintNs, woken early when the phase completes)
 // instead of spinning, so waiting warps leave the issue slots to the warps
-// that verify codes.  Gives up after kWaitNs of global time.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// that verify codes.  Gives up after limit_ns of global time, and in any case
+// after a bounded number of polls (each takes at least a few nanoseconds).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    const uint32_t hint = limit_ns < kWaitHintNs ? static_cast<uint32_t>(limit_ns) : kWaitHintNs;
+    const uint64_t max_polls = limit_ns / 4u + 4096u;
     uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
+    for (uint64_t it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitHintNs)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint)
             : "memory");
         if (ok) return true;
-        if ((it & 63u) == 0) {
+        if ((it & 7u) == 0) {
             const uint64_t now = global_ns();
             if (it == 0) t0 = now;
-            else if (now - t0 > kWaitNs) return false;
+            else if (now - t0 > limit_ns) return false;
         }
+        if (it >= max_polls) return false;
     }
 }
 
@@ -972,12 +1043,14 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
     __shared__ uint32_t s_mask[kMaxTables * 2 * W];
     __shared__ uint32_t s_hist[kStreamWarps][kHistBins];
     __shared__ __align__(8) uint64_t s_bar[kStreamWarps][kStages];
+    __shared__ __align__(8) uint64_t s_never;   // a barrier no copy completes (timeout test)
     build_layout(a.tables, a.m, W, s_len, s_mask);
     for (int i = threadIdx.x; i < kStreamWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     if (lane == 0) {
         for (int i = 0; i < kStages; ++i) mbar_init(&s_bar[warp][i], 1);
+        if (warp == 0) mbar_init(&s_never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -1024,20 +1097,29 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
     constexpr int kPer = static_cast<int>(stage_entries<W, REDUCED>());
     constexpr int B = kPer / 32 < 4 ? kPer / 32 : 4;
     constexpr int R = 2 * W - 1;
-    constexpr int BR = REDUCED && W == 1 ? 8 : 4;   // records per lane at a time
     int b = 0;
     uint32_t unique = 0;
+    bool first_wait = true;
     while (cur.valid) {
         unsigned char* const slot_b = slot0 + b * kStageSlot;
         uint64_t* const bar_b = bar0 + b;
-        if (!mbar_wait_bounded(bar_b, (parities >> b) & 1u)) {
+        // With the timeout test on, the warp's first wait is on a barrier that
+        // no copy completes, so it runs out after a.wait_ns (its copies stay
+        // issued and are drained below).  The decision is warp-uniform.
+        const bool ok_lane = (a.wait_test && first_wait) ? mbar_wait_bounded(&s_never, 0u, a.wait_ns)
+                                                          : mbar_wait_bounded(bar_b, (parities >> b) & 1u, a.wait_ns);
+        first_wait = false;
+        if (!__all_sync(0xFFFFFFFFu, ok_lane)) {
             if (lane == 0) atomicExch(a.timeout, 1);
-            // let this warp's other copies land before leaving
+            // every copy this warp issued (slot b's and the stages after it)
+            // lands before the warp leaves, each waited for with the full limit
+            mbar_wait_bounded(bar_b, (parities >> b) & 1u, kWaitNs);
             for (int i = 1; i < kStages; ++i) {
                 const bool issued = i == 1 ? n1.valid : (i == 2 ? n2.valid : n3.valid);
                 const int bi = (b + i) % kStages;
-                if (issued) mbar_wait_bounded(bar0 + bi, (parities >> bi) & 1u);
+                if (issued) mbar_wait_bounded(bar0 + bi, (parities >> bi) & 1u, kWaitNs);
             }
+            __syncwarp();
             return;
         }
         parities ^= 1u << b;
@@ -1056,22 +1138,57 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
                 th[i] = static_cast<uint32_t>(rho) + (i < j ? 1u : 0u);
             }
             const bool count_new = 2 * W * rho + j > cur.hd;
-            const uint32_t* sr = reinterpret_cast<const uint32_t*>(slot_b) + cur.shift * R;
             const uint32_t* ids = a.tables[j].ids;
-            for (uint32_t base = 0; base < cur.cnt; base += 32 * BR) {
-                uint32_t pos[BR];
-                bool valid[BR];
-                uint32_t rec[BR][R];
+            const int far = (cur.bnd < 0 || a.exact_stats) ? 0x7FFFFFFF : cur.bnd;
+            // The slot holds records [0, shift + cnt) of the copy, the stage's
+            // own from `shift` on.  Lane l reads group g = l, l + 32, ... of
+            // four records with R 16-byte loads; only groups that hold a
+            // stage record are read.
+            const uint4* sg = reinterpret_cast<const uint4*>(slot_b);
+            const uint32_t r_lo = cur.shift, r_hi = cur.shift + cur.cnt;
+            const uint32_t ngroups = (r_hi + 3u) / 4u;
+            for (uint32_t g0 = 0; g0 < ngroups; g0 += 32) {
+                const uint32_t g = g0 + lane;
+                uint32_t wv[4 * R];
+                if (g < ngroups) {
 #pragma unroll
-                for (int k = 0; k < BR; ++k) {
-                    const uint32_t i = base + k * 32 + lane;
-                    valid[k] = i < cur.cnt;
-                    pos[k] = cur.pos + i;
+                    for (int r = 0; r < R; ++r) {
+                        const uint4 v = sg[g * R + r];
+                        wv[4 * r] = v.x;
+                        wv[4 * r + 1] = v.y;
+                        wv[4 * r + 2] = v.z;
+                        wv[4 * r + 3] = v.w;
+                    }
+                } else {
 #pragma unroll
-                    for (int w = 0; w < R; ++w) rec[k][w] = valid[k] ? sr[i * R + w] : 0u;
+                    for (int r = 0; r < 4 * R; ++r) wv[r] = 0u;
                 }
-                process_records<R, MODE, BR>(a, whist, cur.q, j, rho, cur.bnd, count_new, gq, th, ids, pos, valid,
-                                             rec, unique);
+                // Distances first: a record farther than the query's bound is
+                // never stored nor counted (far = no limit without a bound),
+                // and nearly every record is, so the warp goes on to the
+                // duplicate test and the stores only when a lane has a near one.
+                bool valid[4];
+                uint32_t near = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t ri = 4u * g + k;
+                    valid[k] = ri >= r_lo && ri < r_hi;
+                    int d = rho;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) d += __popc(wv[k * R + i] ^ gq[i]);
+                    near |= (valid[k] && d <= far) ? (1u << k) : 0u;
+                }
+                if (!__any_sync(0xFFFFFFFFu, near != 0u)) continue;
+                uint32_t pos[4];
+                uint32_t rec[4][R];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    pos[k] = cur.pos + (4u * g + k - r_lo);
+#pragma unroll
+                    for (int i = 0; i < R; ++i) rec[k][i] = wv[k * R + i];
+                }
+                process_records<R, MODE, 4>(a, whist, cur.q, j, rho, cur.bnd, count_new, gq, th, ids, pos, valid,
+                                            rec, unique);
             }
         } else {
         const CandSource src{nullptr, a.tables[j].ids, false};
@@ -1507,9 +1624,37 @@ __global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __res
         b = __shfl_sync(0xFFFFFFFFu, b, 0);
         e = __shfl_sync(0xFFFFFFFFu, e, 0);
         const uint32_t end = min(e, b + probe);
+        if (t.codes && t.rec_words != 0) {
+            // Inline records (every substring one 32-bit word): the table's own
+            // word equals the query's in its own bucket, so the distance is the
+            // popcount over the record's words (the code's other words), and a
+            // code filed under the query's key in table jj < j has record word
+            // jj equal to the query's.
+            constexpr int R = 2 * W - 1;
+            uint32_t g32[2 * W], gq[R];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                g32[2 * w] = static_cast<uint32_t>(g.w[w]);
+                g32[2 * w + 1] = static_cast<uint32_t>(g.w[w] >> 32);
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) gq[i] = i < j ? g32[i] : g32[i + 1];
+            const uint32_t* rec = reinterpret_cast<const uint32_t*>(t.codes);
+            for (uint32_t p = b + lane; p < end; p += 32) {
+                int d = 0;
+                bool first = true;
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const uint32_t x = __ldg(rec + static_cast<uint64_t>(p) * R + i) ^ gq[i];
+                    d += __popc(x);
+                    if (i < j && x == 0u) first = false;
+                }
+                if (first) atomicAdd(&h[d], 1u);
+            }
+            continue;
+        }
         for (uint32_t p = b + lane; p < end; p += 32) {
-            const Code<W> c = (t.codes && t.rec_words == 0) ? load_code<W>(t.codes, p)
-                                                            : load_code<W>(codes, __ldg(t.ids + p));
+            const Code<W> c = t.codes ? load_code<W>(t.codes, p) : load_code<W>(codes, __ldg(t.ids + p));
             // a code also filed under the query's key in an earlier table is
             // counted there or not at all: the count never exceeds the number
             // of distinct codes, so the bound stays valid
@@ -1628,12 +1773,16 @@ mih_status search_cfg(const GridCfg** out) {
 }
 
 template <int W, int MODE, bool ALIGNED>
-mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch) {
+mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch, bool spans) {
     const GridCfg* cfg = nullptr;
     MIH_TRY((search_cfg<W, MODE, ALIGNED>(&cfg)));
     if (!launch) return MIH_OK;
-    search_kernel<W, MODE, ALIGNED><<<dev.sms * cfg->bps, kSearchThreads, 0, s>>>(a);
-    MIH_LAUNCH_CHECK();
+    {
+        KernelSpan ks(s, MIH_PROF_CHUNK, spans);
+        search_kernel<W, MODE, ALIGNED><<<dev.sms * cfg->bps, kSearchThreads, 0, s>>>(a);
+        MIH_LAUNCH_CHECK();
+    }
+    KernelSpan ks(s, MIH_PROF_SLICE, spans);
     if (a.inline_codes) {
         search_stream_kernel<W, MODE, ALIGNED>
             <<<dev.sms * cfg->bps_stream, kStreamWarps * 32, stream_smem_bytes(), s>>>(a);
@@ -1645,17 +1794,20 @@ mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStre
 }
 
 template <int W, int MODE>
-mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch) {
+mih_status launch_search_w(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch, bool spans) {
     // every substring is one whole 32-bit word exactly when m = 2W
-    if (a.m == 2 * W) return launch_search_wa<W, MODE, true>(a, dev, s, launch);
-    return launch_search_wa<W, MODE, false>(a, dev, s, launch);
+    if (a.m == 2 * W) return launch_search_wa<W, MODE, true>(a, dev, s, launch, spans);
+    return launch_search_wa<W, MODE, false>(a, dev, s, launch, spans);
 }
 
+// Launches the chunk and slice kernels (launch = false: only their one-time
+// configuration); spans = per-kernel timing events (never while capturing).
 template <int MODE>
-mih_status launch_search(const SearchArgs& a, int W, const DeviceInfo& dev, cudaStream_t s, bool launch = true) {
-    if (W == 1) return launch_search_w<1, MODE>(a, dev, s, launch);
-    if (W == 2) return launch_search_w<2, MODE>(a, dev, s, launch);
-    return launch_search_w<4, MODE>(a, dev, s, launch);
+mih_status launch_search(const SearchArgs& a, int W, const DeviceInfo& dev, cudaStream_t s, bool launch = true,
+                         bool spans = false) {
+    if (W == 1) return launch_search_w<1, MODE>(a, dev, s, launch, spans);
+    if (W == 2) return launch_search_w<2, MODE>(a, dev, s, launch, spans);
+    return launch_search_w<4, MODE>(a, dev, s, launch, spans);
 }
 
 #ifndef MIH_BIG_CAP_LOG2
@@ -1707,19 +1859,23 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
                     const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr) {
     const bool in_graph = cs != nullptr;
     cudaStream_t s = in_graph ? cs : ws.stream();
-    if (static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
-        plan_scan_kernel<<<1, kPlanThreads, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
-                                                    p.chunk_off, p.counters);
-        MIH_LAUNCH_CHECK();
-    } else {
-        plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
-                                                          p.chunk_off);
-        MIH_LAUNCH_CHECK();
-        if (in_graph)
-            MIH_TRY(scan_exclusive_u64_pre(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, p.scan_tmp, s));
-        else
-            MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
-        MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
+    {
+        KernelSpan plan_span(s, MIH_PROF_PLAN, !in_graph);
+        if (static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
+            plan_scan_kernel<<<1, kPlanThreads, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
+                                                        p.chunk_off, p.counters);
+            MIH_LAUNCH_CHECK();
+        } else {
+            plan_chunks_kernel<<<grid1(a.nq + 1), 256, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi,
+                                                              a.exh, p.chunk_off);
+            MIH_LAUNCH_CHECK();
+            if (in_graph)
+                MIH_TRY(scan_exclusive_u64_pre(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, p.scan_tmp,
+                                               s));
+            else
+                MIH_TRY(scan_exclusive_u64(p.chunk_off, p.chunk_off, static_cast<size_t>(a.nq) + 1, ws));
+            MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
+        }
     }
     a.t_lo = t_lo;
     a.t_hi = t_hi;
@@ -1731,9 +1887,11 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
     a.big_next = a.big_count + 1;
     a.inline_codes = ix->inline_codes ? 1 : 0;
     a.timeout = p.timeout;
+    a.wait_ns = wait_limit_ns();
+    a.wait_test = wait_test_expire() ? 1 : 0;
     if (in_graph) return launch_search<MODE>(a, ix->W, dev, s);   // events cannot sit in a loop body
     main_kernel_begin(s);
-    const mih_status st = launch_search<MODE>(a, ix->W, dev, s);
+    const mih_status st = launch_search<MODE>(a, ix->W, dev, s, true, true);
     main_kernel_end(s);
     return st;
 }
@@ -1933,8 +2091,11 @@ mih_status launch_select(const SelectInputs& in, Workspace& ws) {
     a.out_ids = in.out_ids;
     a.out_dist = in.out_dist;
     a.err = err;
-    select_kernel<<<in.nq, 256, smem, ws.stream()>>>(a);
-    MIH_LAUNCH_CHECK();
+    {
+        KernelSpan ks(ws.stream(), MIH_PROF_SELECT);
+        select_kernel<<<in.nq, 256, smem, ws.stream()>>>(a);
+        MIH_LAUNCH_CHECK();
+    }
     int herr = 0;
     MIH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ws.stream()));
     MIH_CUDA(cudaStreamSynchronize(ws.stream()));
@@ -2028,6 +2189,9 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_TRY(ws.alloc(&buf1, static_cast<size_t>(nq) * cap));
     MIH_TRY(ws.alloc(&qstats, 4ull * nq));
     MIH_TRY(ws.alloc(&active, 1));
+    unsigned long long* sliced;
+    MIH_TRY(ws.alloc(&sliced, 1));
+    MIH_CUDA(cudaMemsetAsync(sliced, 0, sizeof(unsigned long long), s));
     uint8_t* exh;
     MIH_TRY(ws.alloc(&exh, nq));
     MIH_CUDA(cudaMemsetAsync(exh, 0, nq, s));
@@ -2042,6 +2206,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     if (ix->n > 0 && query_stats == nullptr && ix->probe > 0) {
         // (with per-query counters requested the steps run exactly as Alg. 3
         // counts them, from a histogram-only start)
+        KernelSpan ks(s, MIH_PROF_PROBE);
         const unsigned blocks = (nq + 7) / 8;
         if (ix->W == 1)
             bound_probe_kernel<1><<<blocks, 256, 0, s>>>(ix->dev_tables, ix->m, qb, ix->codes, queries, nq, ix->n, k,
@@ -2075,6 +2240,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     a.hist_done = hist_done;
     a.n = ix->n;
     a.exact_stats = query_stats != nullptr ? 1 : 0;
+    a.sliced = sliced;
 
     // One wave: every active query runs its current Alg. 3 step(s), then the
     // stopping test advances or retires it.  cs = capture stream (graph) or 0.
@@ -2082,6 +2248,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         cudaStream_t ws_s = cs ? cs : s;
         MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs));
         MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), ws_s));
+        KernelSpan ks(ws_s, MIH_PROF_STOP, cs == nullptr);
         knn_stop_kernel<<<grid1(32ull * nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
                                                     hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
                                                     exh, budget);
@@ -2091,7 +2258,9 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     // At most q + 1 waves: step t <= q reaches every code (Prop. 1 with r = q).
     const unsigned int max_waves = static_cast<unsigned int>(qb) + 1;
     uint64_t waves = 0;
-    if (ix->n > 0 && ix->executor == MIH_EXEC_HOST) {
+    // per-kernel timing runs the waves from the host so that each launch can be
+    // bracketed by events (same kernels, same results)
+    if (ix->n > 0 && (ix->executor == MIH_EXEC_HOST || timing_level() >= 2)) {
         for (unsigned int w = 0; w < max_waves; ++w) {
             MIH_TRY(wave(nullptr));
             ++waves;
@@ -2164,6 +2333,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         b.qstats = nullptr;
         b.hist_done = nullptr;
         b.err = err;
+        b.sliced = nullptr;
         MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
         ++waves;
         MIH_TRY(check_timeout(plan, s));
@@ -2171,6 +2341,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     }
     if (ix->inline_codes && ix->n > 0) {
         const unsigned blocks = nq < static_cast<uint32_t>(dev.sms) * 16u ? nq : static_cast<unsigned>(dev.sms) * 16u;
+        KernelSpan ks(s, MIH_PROF_RESOLVE);
         resolve_ids_kernel<<<blocks, 256, 0, s>>>(buf1, cnt1, cap, nq, ix->dev_tables, dk);
         MIH_LAUNCH_CHECK();
     }
@@ -2208,6 +2379,10 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         }
         stats->phase2_queries = hover;
         stats->waves = waves;
+        unsigned long long hs = 0;
+        MIH_CUDA(cudaMemcpyAsync(&hs, sliced, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        MIH_CUDA(cudaStreamSynchronize(s));
+        stats->candidates_sliced = hs;
     }
     MIH_CUDA(cudaStreamSynchronize(s));
     return MIH_OK;
@@ -2264,6 +2439,10 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
     a.qstats = qstats;
     a.n = ix->n;
     a.exact_stats = query_stats != nullptr ? 1 : 0;
+    unsigned long long* sliced;
+    MIH_TRY(ws.alloc(&sliced, 1));
+    MIH_CUDA(cudaMemsetAsync(sliced, 0, sizeof(unsigned long long), s));
+    a.sliced = sliced;
     uint8_t* exh;
     MIH_TRY(ws.alloc(&exh, nqa));
     {
@@ -2311,6 +2490,10 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
                 stats->steps += ix->n > 0 ? static_cast<uint64_t>(reff) + 1 : 0;
             }
             stats->waves = ix->n > 0 ? 1 : 0;
+            unsigned long long hs = 0;
+            MIH_CUDA(cudaMemcpyAsync(&hs, sliced, sizeof(hs), cudaMemcpyDeviceToHost, s));
+            MIH_CUDA(cudaStreamSynchronize(s));
+            stats->candidates_sliced = hs;
         }
         MIH_CUDA(cudaStreamSynchronize(s));
         return MIH_OK;
@@ -2338,6 +2521,7 @@ mih_status mih_rnear(const mih_index* ix, const uint64_t* queries, uint32_t nq, 
         b.out_base = off64;
         b.qstats = nullptr;
         b.err = err;
+        b.sliced = nullptr;
         MIH_TRY(run_wave<kModeCollect>(ix, b, plan, t_lo, t_hi, dev, ws));
         MIH_TRY(check_timeout(plan, s));
         MIH_TRY(check_flag(err, "mih_rnear: fill pass found more results than the count pass", s));

@@ -107,3 +107,58 @@ def test_suggest_m_table4(lib):
     assert lib.mih_suggest_m(64, 10**9) == 2
     assert lib.mih_suggest_m(128, 10**9) == 4
     assert lib.mih_suggest_m(256, 10**9) == 9   # 8.56 rounds to 9; the paper's CV picked 8
+
+
+def _layout_cost(q, n, m, w, lengths):
+    """Cost of a layout under Eq. 7 applied per table over Alg. 3's schedule:
+    table j searches rings 0..(t - j) // m after step t (none when t < j)."""
+    from math import comb
+
+    total = 0.0
+    for j, s in enumerate(lengths):
+        rings = sum(wt * sum(comb(s, r) for r in range((t - j) // m + 1)) for t, wt in enumerate(w) if t >= j)
+        total += (1 + n / 2**s) * rings
+    return total
+
+
+def _compositions(q, m, lo=1, hi=32):
+    if m == 1:
+        if lo <= q <= hi:
+            yield (q,)
+        return
+    for s in range(lo, min(hi, q - lo * (m - 1)) + 1):
+        for rest in _compositions(q - s, m - 1, lo, hi):
+            yield (s,) + rest
+
+
+@pytest.mark.parametrize("q,n,m,w", [(24, 10**5, 3, [0, 0, 0, 0, 1]), (20, 10**4, 2, [0, 0, 0, 1]),
+                                     (30, 10**6, 4, [0.1, 0.2, 0.3, 0.1, 0.1, 0.2, 0.4, 0.1]),
+                                     (40, 10**7, 5, [0] * 7 + [1]), (16, 200, 3, [1, 1, 1, 1, 1, 1])])
+def test_cost_layout_is_the_minimum(lib, q, n, m, w):
+    """mih_cost_layout returns a layout whose cost is the minimum over every
+    composition of q into m lengths of 1..32 (brute force)."""
+    lengths, cost = lib.mih_cost_layout(q, n, m, w)
+    assert len(lengths) == m and sum(lengths) == q and all(1 <= s <= 32 for s in lengths)
+    assert cost == pytest.approx(_layout_cost(q, n, m, w, lengths), rel=1e-9)
+    best = min(_layout_cost(q, n, m, w, c) for c in _compositions(q, m))
+    assert cost == pytest.approx(best, rel=1e-9)
+
+
+def test_cost_layout_reduces_to_eq7(lib):
+    """Where every table searches the same rings (stop step t = m r' + m - 1)
+    and the layout is forced (m = q/32), the per-table model is Eq. 7."""
+    for q, n, r in [(64, 10**9, 3), (128, 10**9, 2), (256, 10**8, 1), (128, 10**6, 0)]:
+        m = q // 32
+        t = m * r + m - 1
+        lengths, cost = lib.mih_cost_layout(q, n, m, [0] * t + [1])
+        assert lengths == [32] * m
+        assert cost == pytest.approx(lib.mih_cost_model(q, n, 32, t), rel=1e-12)
+
+
+def test_cost_layout_rejects_bad_arguments(lib):
+    with pytest.raises(lib.MihError):
+        lib.mih_cost_layout(128, 10**6, 3, [1])          # 3 tables cannot hold 128 bits
+    with pytest.raises(lib.MihError):
+        lib.mih_cost_layout(64, 10**6, 2, [1, -1])       # negative weight
+    with pytest.raises(lib.MihError):
+        lib.mih_cost_layout(64, 10**6, 2, [])

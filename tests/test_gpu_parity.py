@@ -41,6 +41,33 @@ def perturb(codes, flips, seed):
     return np.packbits(bits, axis=1, bitorder="little").view(np.uint64).reshape(len(codes), -1)
 
 
+def planted(n, q, seed, nq, per_word, pool=8, fmin=None, fmax=None):
+    """Clusters around `pool` random centres.  A database code is a centre with
+    fmin..fmax random bits flipped; a query is a centre with `per_word` bits
+    flipped in every 32-bit word.  So in table j (m = q/32, one word per table)
+    the bucket of the centre's word holds the cluster members that kept word j
+    (hundreds of codes, above the slice threshold) and lies at ring per_word
+    from the query, and the k-th distance (about q/32 * per_word + fmin) keeps
+    the query running until it reaches that ring in several tables."""
+    rng = np.random.default_rng(seed)
+    W32 = q // 32
+    fmin = 1 if fmin is None else fmin
+    fmax = W32 + 4 if fmax is None else fmax
+    cent = synth.uniform_codes(pool, q, seed + 100)
+    db = cent[rng.integers(0, pool, n)].copy()
+    dw = db.view(np.uint32).reshape(n, W32)
+    for i, f in enumerate(rng.integers(fmin, fmax + 1, n)):
+        for b in rng.choice(q, size=f, replace=False):
+            dw[i, b // 32] ^= np.uint32(1) << np.uint32(b % 32)
+    qs = cent[rng.integers(0, pool, nq)].copy()
+    qw = qs.view(np.uint32).reshape(nq, W32)
+    for i in range(nq):
+        for j in range(W32):
+            for b in rng.choice(32, size=per_word, replace=False):
+                qw[i, j] ^= np.uint32(1) << np.uint32(b)
+    return db, qs
+
+
 def workload(kind, q, n, nq, seed=0):
     if kind == "uniform":
         return synth.uniform_codes(n, q, seed), synth.uniform_codes(nq, q, seed + 1)
@@ -52,7 +79,7 @@ def workload(kind, q, n, nq, seed=0):
 
 # (kind, q, n, nq, m list) -- sizes span many chunks/tiles with ragged tails
 KNN_CASES = [
-    ("uniform", 64, 100_000, 300, [4, 3]),
+    ("uniform", 64, 100_000, 300, [4, 3, 2]),
     ("lsh", 128, 200_003, 257, [6, 4, 5]),
     ("lsh", 256, 60_001, 130, [9, 8, 12]),
     ("ties", 128, 30_000, 100, [4, 6]),
@@ -118,6 +145,46 @@ def test_mih_work_counters_match_alg3(gpu_lib, orc, kind, q, m, n):
             assert tuple(st[i]) == tuple(cnt), (i, k, st[i], cnt)
 
 
+@pytest.mark.parametrize("q,per_word,fmin,fmax", [(64, 3, 1, 5), (128, 3, 2, 8), (256, 2, 2, 8)])
+def test_record_path_counters_reach_ring_2(gpu_lib, orc, q, per_word, fmin, fmax):
+    """Alg. 3 counters of the inline-record path at rings rho >= 2.
+
+    m = q/32: every substring is one 32-bit word, and the tables keep records
+    without their own word.  A record reached at ring rho is kept only if every
+    other word i differs from the query in at least rho + [i < j] bits (the
+    first-discoverer reading of Sec. 6's duplicate removal).  The planted
+    clusters put buckets of hundreds of codes (streamed by the slice kernel) at
+    ring per_word >= 2 of every table, and the k-th distance is large enough
+    that queries reach them.  Per-query lookups, raw and unique candidates and
+    the last step must equal the oracle's Alg. 3; the results must equal the
+    oracle with and without per-query counters."""
+    mih = gpu_lib
+    m = q // 32
+    db, qs = planted(4000, q, 9, 24, per_word, fmin=fmin, fmax=fmax)
+    queries = to_dev(qs)
+    mo = orc.MihOracle(db, q, m)
+    ixs = [mih.mih_build(to_dev(db), q, m, scan_factor=-1, inline_codes=il) for il in (1, -1)]
+    info = ixs[0].info()
+    assert info["inline_codes"] == 1 and max(info["max_bucket"]) > 64
+    last = []
+    for k in (1, 25):
+        want_ids, want_dist = orc.knn(db, qs, k)
+        for ix in ixs:
+            r = mih.mih_knn(ix, queries, k, query_stats=True)
+            st = host(r["query_stats"])
+            for i in range(len(qs)):
+                ids, dist, cnt = mo.knn(qs[i], k)
+                assert np.array_equal(ids_of(r["ids"])[i], ids) and np.array_equal(host(r["dist"])[i], dist)
+                assert tuple(st[i]) == tuple(cnt), (i, k, st[i], cnt)
+            last.extend(int(x) for x in st[:, 3])
+            fast = mih.mih_knn(ix, queries, k)
+            assert np.array_equal(ids_of(fast["ids"]), want_ids) and np.array_equal(host(fast["dist"]), want_dist)
+    # the last step t = m * rho + j reached ring rho >= 2
+    assert max(last) >= 2 * m, max(last)
+    for ix in ixs:
+        ix.free()
+
+
 @pytest.mark.parametrize("kind,q,m,n", [("lsh", 128, 6, 200_003), ("uniform", 64, 3, 50_000),
                                         ("lsh", 256, 9, 60_001)])
 def test_graph_and_host_executors_agree(gpu_lib, orc, kind, q, m, n):
@@ -159,7 +226,7 @@ def test_per_query_k_and_padding(gpu_lib, orc):
         assert np.array_equal(host(r["dist"]), want_dist)
 
 
-@pytest.mark.parametrize("q,m", [(64, 4), (128, 6), (256, 12)])
+@pytest.mark.parametrize("q,m", [(64, 4), (64, 2), (128, 6), (128, 4), (256, 12), (256, 8)])
 def test_rnear_matches_oracle(gpu_lib, orc, q, m):
     mih = gpu_lib
     db, qs = workload("lsh", q, 40_000, 50, seed=21)
@@ -288,6 +355,110 @@ def test_big_buckets_streamed_and_gathered(gpu_lib, orc, q):
             got = mih.mih_rnear(ix, queries, 3)
             assert np.array_equal(ids_of(got["ids"]), wid) and np.array_equal(host(got["dist"]), wd)
             ix.free()
+
+
+@pytest.mark.parametrize("q,m,executor", [(128, 4, 2), (128, 5, 2), (64, 2, 1)])
+def test_bounded_wait_timeout_path(gpu_lib, orc, q, m, executor):
+    """A bounded wait on a bulk copy that runs out ends the call with
+    MIH_ETIMEOUT, and the same index answers exactly afterwards.
+
+    The wait is made to run out without any fault: with the test switch of
+    mih_set_wait_limit each warp of the slice kernel makes its first wait on a
+    barrier that no copy completes (limit 200 us); the warp then drains its own
+    copies before leaving.  Big buckets (20 patterns x 2500 copies) make sure
+    the slice kernel runs; m = q/32 streams records, m = 5 whole codes."""
+    mih = gpu_lib
+    rng = np.random.default_rng(91)
+    pats = synth.uniform_codes(20, q, 90)
+    db = np.concatenate([np.repeat(pats, 2500, axis=0), synth.uniform_codes(10_001, q, 92)])
+    db = db[rng.permutation(len(db))]
+    qs = np.concatenate([perturb(pats[:6], 2, 93), synth.uniform_codes(4, q, 94)])
+    codes, queries = to_dev(db), to_dev(qs)
+    ix = mih.mih_build(codes, q, m, inline_codes=1, executor=executor)
+    try:
+        mih.mih_set_wait_limit(200, True)
+        for call in (lambda: mih.mih_knn(ix, queries, 10), lambda: mih.mih_rnear(ix, queries, 3)):
+            with pytest.raises(mih.MihError) as e:
+                call()
+            assert e.value.status == mih.MIH_ETIMEOUT, str(e.value)
+    finally:
+        mih.mih_set_wait_limit(0, False)
+    want_ids, want_dist = orc.knn(db, qs, 10)
+    r = mih.mih_knn(ix, queries, 10)
+    assert np.array_equal(ids_of(r["ids"]), want_ids) and np.array_equal(host(r["dist"]), want_dist)
+    woff, wid, wd = orc.rnear(db, qs, 3)
+    got = mih.mih_rnear(ix, queries, 3)
+    assert np.array_equal(ids_of(got["ids"]), wid) and np.array_equal(host(got["dist"]), wd)
+    ix.free()
+
+
+UNEVEN_CASES = [
+    ("lsh", 128, [29, 24, 25, 25, 25], 100_003),
+    ("uniform", 64, [22, 23, 19], 50_000),
+    ("lsh", 256, [31, 31, 31, 27, 27, 27, 27, 27, 28], 30_001),
+    ("ties", 128, [30, 26, 24, 24, 24], 5_000),
+    ("lsh", 128, [16, 32, 32, 24, 24], 60_000),
+]
+
+
+@pytest.mark.parametrize("kind,q,lengths,n", UNEVEN_CASES)
+def test_per_table_lengths_match_oracle(gpu_lib, orc, kind, q, lengths, n):
+    """Per-table substring lengths (open in the Conclusion): results equal the
+    definition, and the Alg. 3 counters equal the oracle's over the same
+    partition (Props. 1-2 hold for any disjoint partition)."""
+    mih = gpu_lib
+    m = len(lengths)
+    db, qs = workload(kind, q, n, 97, seed=71)
+    codes, queries = to_dev(db), to_dev(qs)
+    ix = mih.mih_build(codes, q, m, substring_length=lengths)
+    info = ix.info()
+    assert info["substring_length"] == lengths
+    assert info["substring_offset"] == [int(x) for x in np.concatenate([[0], np.cumsum(lengths)[:-1]])]
+    for k in (1, 10, 100):
+        want_ids, want_dist = orc.knn(db, qs, k)
+        r = mih.mih_knn(ix, queries, k)
+        assert np.array_equal(ids_of(r["ids"]), want_ids), k
+        assert np.array_equal(host(r["dist"]), want_dist), k
+    woff, wid, wd = orc.rnear(db, qs, q // 16)
+    got = mih.mih_rnear(ix, queries, q // 16)
+    assert np.array_equal(ids_of(got["ids"]), wid) and np.array_equal(host(got["dist"]), wd)
+    ix.free()
+    # Alg. 3 counters on a smaller database
+    small = db[:min(n, 8000)]
+    mo = orc.MihOracle(small, q, m, lengths=lengths)
+    ixs = mih.mih_build(to_dev(small), q, m, substring_length=lengths, scan_factor=-1)
+    r = mih.mih_knn(ixs, to_dev(qs[:24]), 10, query_stats=True)
+    st = host(r["query_stats"])
+    for i in range(24):
+        ids, dist, cnt = mo.knn(qs[i], 10)
+        assert np.array_equal(ids_of(r["ids"])[i], ids) and np.array_equal(host(r["dist"])[i], dist)
+        assert tuple(st[i]) == tuple(cnt), (i, st[i], cnt)
+    ixs.free()
+
+
+def test_per_table_lengths_are_validated(gpu_lib):
+    mih = gpu_lib
+    codes = to_dev(synth.uniform_codes(1000, 128, 3))
+    for m, ln in ((5, [30, 30, 30, 30, 9]), (4, [33, 31, 32, 32]), (5, [32, 32, 32, 32, 0]), (3, [64, 32, 32])):
+        with pytest.raises(mih.MihError) as e:
+            mih.mih_build(codes, 128, m, substring_length=ln)
+        assert e.value.status == mih.MIH_EINVAL
+
+
+def test_autotune_layout(gpu_lib, orc):
+    """The layout autotuner times the Sec. 2.1 layout against the cost-model
+    layout for the measured stop steps and returns a valid partition; the
+    index built on it is exact."""
+    mih = gpu_lib
+    db, _ = workload("lsh", 128, 300_000, 1)
+    hold = synth.lsh_codes(400, 128, 9)
+    lengths, times = mih.mih_autotune_layout(to_dev(db), 128, to_dev(hold), 50, 5)
+    assert len(lengths) == 5 and sum(lengths) == 128 and all(1 <= s <= 32 for s in lengths)
+    assert times["uniform"] > 0 and times["cost_model"] > 0
+    ix = mih.mih_build(to_dev(db), 128, 5, substring_length=lengths)
+    want_ids, want_dist = orc.knn(db, hold[:60], 50)
+    r = mih.mih_knn(ix, to_dev(hold[:60]), 50)
+    assert np.array_equal(ids_of(r["ids"]), want_ids) and np.array_equal(host(r["dist"]), want_dist)
 
 
 def test_autotune_picks_a_candidate(gpu_lib, orc):

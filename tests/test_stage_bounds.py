@@ -1,10 +1,13 @@
 """Bounds of the slice kernel's bulk copies, checked on the host for every
 entry layout: each copy starts and ends on 16-byte boundaries, covers the
-stage's entries, fits its 4112-byte shared-memory slot, and reads at most 16
+stage's entries, fits its 4112-byte shared-memory slot (as do the 16-byte
+group loads that read records out of it), and reads at most 16
 bytes past the last entry (the padding the build adds after each table's
 inline codes).  The arithmetic restates the kernel's stage sizing (4 KB
 stages: 8W-byte codes, or 4(2W-1)-byte records rounded down to whole warp
-rows) so that a change to one is checked against the other by review."""
+rows).  The slot bound is also a static_assert in the kernel source over the
+stage size it is compiled with, so a build with another stage size or
+another copy rule that overruns a slot does not compile."""
 import numpy as np
 import pytest
 
@@ -12,7 +15,9 @@ STAGE, SLOT = 4096, 4096 + 16
 
 
 def stage_entries(W, reduced):
-    return ((STAGE // (4 * (2 * W - 1))) & ~31) if reduced else STAGE // (8 * W)
+    # records: whole groups of four (16 (2W - 1) bytes) in a stage, less the
+    # three records a copy may start early
+    return 4 * (STAGE // (16 * (2 * W - 1))) - 3 if reduced else STAGE // (8 * W)
 
 
 def copy_of(W, reduced, pos, cnt):
@@ -31,7 +36,7 @@ def copy_of(W, reduced, pos, cnt):
 def test_stage_copies_stay_in_bounds(W, reduced):
     rng = np.random.default_rng(W * 10 + reduced)
     per = stage_entries(W, reduced)
-    assert per % 32 == 0 and per > 0
+    assert per >= 32 and (reduced or per % 32 == 0)
     for n in (1, 2, 3, 5, 97, 1024, 100_003):
         for _ in range(300):
             pos = int(rng.integers(0, n))
@@ -42,5 +47,10 @@ def test_stage_copies_stay_in_bounds(W, reduced):
             # the stage's entries lie inside the copy
             assert start <= pos * eb and (pos + cnt) * eb <= start + nbytes
             assert shift * eb == pos * eb - start
+            if reduced:
+                # lanes read whole groups of four records (16-byte loads) that
+                # hold a stage record: all inside the slot
+                groups = (shift + cnt + 3) // 4
+                assert groups * 4 * eb <= SLOT and (4 * eb) % 16 == 0
             # at most 16 bytes past the end of the table's n entries
             assert start + nbytes <= n * eb + 16

@@ -1,19 +1,36 @@
-"""Full-size sampled parity: the benchmark's configurations (1e9 codes, 10^4
-queries in one call, the default graph executor) checked against the oracle
-on a few queries spread over the batch, which the oracle answers over all 1e9
-codes.  The linear scan is checked on the same queries.  Collected after the
-other GPU tests (a minute or two per case: generation, build, and the oracle's
-pass over 16 GB of codes)."""
+"""Full-size sampled parity: the benchmark's configurations (10^4 queries in
+one call, the default graph executor) checked against the oracle on queries
+spread over the batch, which the oracle answers over every code of the
+database.  The linear scan is checked on the same queries.  Collected after
+the other GPU tests (a minute or two per case: generation, build, and the
+oracle's pass over up to 32 GB of codes).
+
+Configurations:
+- 1e9 x 128-bit LSH-style codes, k = 100, m = 4 (inline records);
+- 1e9 x 64-bit uniform codes, per-query k log-uniform in [1, 1000], m = 3;
+- 1e9 x 256-bit LSH-style codes, per-query k log-uniform in [1, 1000], m = 9:
+  the index keeps no inline codes (they would need 9 x 32 GB), so every
+  candidate is gathered by id;
+- 1e7 x 128-bit LSH-style codes, k = 100, m = 6 (21/21/21/21/22/22-bit
+  substrings), 1000 of the 10^4 queries compared.
+"""
 import numpy as np
 import pytest
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
-N, NQ, SAMPLE = 1_000_000_000, 10_000, 6
+NQ = 10_000
+CASES = [
+    # kind, q, n, m, k, sampled queries, expected inline codes
+    ("lsh", 128, 1_000_000_000, 4, 100, 6, 1),
+    ("uniform", 64, 1_000_000_000, 3, "kper", 6, None),
+    ("lsh", 256, 1_000_000_000, 9, "kper", 6, 0),
+    ("lsh", 128, 10_000_000, 6, 100, 1000, 1),
+]
 
 
-@pytest.mark.parametrize("kind,q,m,k", [("lsh", 128, 4, 100), ("uniform", 64, 3, "kper")])
-def test_full_size_sampled_parity(gpu_lib, orc, kind, q, m, k):
+@pytest.mark.parametrize("kind,q,n,m,k,sample,inline", CASES)
+def test_full_size_sampled_parity(gpu_lib, orc, kind, q, n, m, k, sample, inline):
     import torch
 
     from paper_1307_2982_gb300 import synth
@@ -21,22 +38,25 @@ def test_full_size_sampled_parity(gpu_lib, orc, kind, q, m, k):
     mih = gpu_lib
     dev = torch.device("cuda", 0)
     gen = synth.lsh_codes_torch if kind == "lsh" else synth.uniform_codes_torch
-    codes = gen(N, q, 0, device=dev)
+    codes = gen(n, q, 0, device=dev)
     queries = gen(NQ, q, 1, device=dev)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     ix = mih.mih_build(codes, q, m)
-    rows = np.linspace(0, NQ - 1, SAMPLE).astype(np.int64)
+    if inline is not None:
+        assert ix.info()["inline_codes"] == inline
+    rows = np.linspace(0, NQ - 1, sample).astype(np.int64)
     if k == "kper":
         kq = synth.per_query_k(NQ, seed=3, kmax=1000).astype(np.uint32)
         r = mih.mih_knn(ix, queries, torch.from_numpy(kq.astype(np.int32)).to(dev))
         off = r["offsets"].cpu().numpy()
-        got = [(r["ids"][off[i]:off[i + 1]].cpu().numpy().view(np.uint32),
-                r["dist"][off[i]:off[i + 1]].cpu().numpy()) for i in rows]
+        ids_all, dist_all = r["ids"].cpu().numpy().view(np.uint32), r["dist"].cpu().numpy()
+        got = [(ids_all[off[i]:off[i + 1]], dist_all[off[i]:off[i + 1]]) for i in rows]
         ksample = kq[rows]
     else:
         r = mih.mih_knn(ix, queries, k)
-        got = [(r["ids"][i].cpu().numpy().view(np.uint32), r["dist"][i].cpu().numpy()) for i in rows]
+        ids_all, dist_all = r["ids"].cpu().numpy().view(np.uint32), r["dist"].cpu().numpy()
+        got = [(ids_all[i], dist_all[i]) for i in rows]
         ksample = k
     qsel = queries[torch.from_numpy(rows).to(dev)].contiguous()
     ls = mih.linscan_knn(codes, q, qsel, torch.from_numpy(np.asarray(ksample, dtype=np.int32)).to(dev)
@@ -47,18 +67,21 @@ def test_full_size_sampled_parity(gpu_lib, orc, kind, q, m, k):
     qs = qsel.cpu().numpy().view(np.uint64)
     del codes, queries
     torch.cuda.empty_cache()
-    res = orc.knn(db, qs, ksample, nthreads=min(orc.default_threads(), SAMPLE))
+    res = orc.knn(db, qs, ksample, nthreads=min(orc.default_threads(), sample))
     if k == "kper":
         woff, wids, wdist = res
         lsoff = ls["offsets"].cpu().numpy()
-        for s in range(SAMPLE):
+        ls_ids, ls_dist = ls["ids"].cpu().numpy().view(np.uint32), ls["dist"].cpu().numpy()
+        for s in range(sample):
             want = (wids[woff[s]:woff[s + 1]], wdist[woff[s]:woff[s + 1]])
             assert np.array_equal(got[s][0], want[0]) and np.array_equal(got[s][1], want[1]), s
-            assert np.array_equal(ls["ids"][lsoff[s]:lsoff[s + 1]].cpu().numpy().view(np.uint32), want[0]), s
+            assert np.array_equal(ls_ids[lsoff[s]:lsoff[s + 1]], want[0]), s
+            assert np.array_equal(ls_dist[lsoff[s]:lsoff[s + 1]], want[1]), s
     else:
         wids, wdist = res
-        for s in range(SAMPLE):
-            assert np.array_equal(got[s][0], wids[s]) and np.array_equal(got[s][1], wdist[s]), s
+        bad = [s for s in range(sample)
+               if not (np.array_equal(got[s][0], wids[s]) and np.array_equal(got[s][1], wdist[s]))]
+        assert not bad, bad[:10]
         assert np.array_equal(ls["ids"].cpu().numpy().view(np.uint32), wids)
         assert np.array_equal(ls["dist"].cpu().numpy(), wdist)
     del db

@@ -53,6 +53,24 @@ def test_noalloc_matches_linscan_twice(gpu_lib, kind, q, n):
         assert np.array_equal(dist.cpu().numpy(), want["dist"].cpu().numpy())
 
 
+@pytest.mark.parametrize("n", [0, 37])
+def test_noalloc_small_databases_twice(gpu_lib, n):
+    """n < k: all n codes, then padding (id 0xFFFFFFFF, distance -1); n = 0:
+    padding only.  Both as linscan_knn gives them, on two calls in a row."""
+    mih = gpu_lib
+    q, k = 128, 100
+    codes = _dev(synth.uniform_codes(max(n, 1), q, 11))[:n]
+    for seed, nq in ((12, 33), (13, 5)):
+        queries = _dev(synth.uniform_codes(nq, q, seed))
+        st, ids, dist = _call(mih, codes, q, queries, k)
+        assert st == mih.MIH_OK, mih.mih_last_error()
+        want = mih.linscan_knn(codes, q, queries, k)
+        assert np.array_equal(ids.cpu().numpy(), want["ids"].cpu().numpy())
+        assert np.array_equal(dist.cpu().numpy(), want["dist"].cpu().numpy())
+        assert np.all(ids.cpu().numpy()[:, n:] == -1) and np.all(dist.cpu().numpy()[:, n:] == -1)
+        assert np.all(dist.cpu().numpy()[:, :n] >= 0)
+
+
 def test_noalloc_ties_second_pass_and_limits(gpu_lib):
     mih = gpu_lib
     import torch
