@@ -248,6 +248,28 @@ MIH_API mih_status linscan_knn(const uint64_t *codes, uint64_t n, int q, const u
                        void *stream);
 
 /* ------------------------------------------------------------------------
+ * mih_merge_topk -- exact k-NN over a database split into id ranges (one
+ * index per range, e.g. one per GPU): merges the ranges' answers.  By the
+ * k-NN definition (Sec. 1.1) the k nearest codes of the whole database are
+ * the k smallest (distance, global id) pairs among the ranges' own k nearest,
+ * since the ranges partition the database and (distance, id) is a total order.
+ *
+ * ids, dist   device, [parts][nq][k_in]: part p's answers for every query,
+ *             each row in (distance, id) order with ids relative to the part
+ *             (as mih_knn / linscan_knn give them for a uniform k_in, padding
+ *             id 0xFFFFFFFF / distance -1 last).
+ * id_base     host, parts entries, non-decreasing: the global id of each
+ *             part's id 0 (global ids must stay below 2^32 - 1).
+ * k           results per query, 1 <= k <= MIH_MAX_K; out_ids / out_dist:
+ *             device [nq][k], (distance, global id) order, padded as mih_knn.
+ * 1 <= parts <= 64, 1 <= k_in <= MIH_MAX_K.  Synchronises `stream`.
+ * Errors: MIH_EINVAL, MIH_ECUDA.
+ */
+MIH_API mih_status mih_merge_topk(const uint32_t *ids, const int32_t *dist, uint32_t parts, uint32_t nq,
+                                  uint32_t k_in, const uint32_t *id_base, uint32_t k, uint32_t *out_ids,
+                                  int32_t *out_dist, void *stream);
+
+/* ------------------------------------------------------------------------
  * mih_autotune -- choose the number of substrings m by timing the search on
  * a hold-out set of queries (Sec. 6 "Number of Substrings": estimate the
  * run time for m near q / log2(n) and keep the fastest; Table 4).
@@ -407,10 +429,9 @@ enum {
     MIH_PROF_PROBE = 2,     /* bound_probe_kernel */
     MIH_PROF_PLAN = 3,      /* per-wave chunk planning (counts and their scan) */
     MIH_PROF_STOP = 4,      /* knn_stop_kernel: the stopping test of Alg. 3 */
-    MIH_PROF_SELECT = 5,    /* select_kernel */
-    MIH_PROF_RESOLVE = 6,   /* resolve_ids_kernel */
-    MIH_PROF_SCAN = 7,      /* linscan_kernel */
-    MIH_PROF_KINDS = 8
+    MIH_PROF_SELECT = 5,    /* select_kernel (with the ids of table positions) */
+    MIH_PROF_SCAN = 6,      /* linscan_kernel */
+    MIH_PROF_KINDS = 7
 };
 
 typedef struct {
@@ -428,6 +449,35 @@ MIH_API void mih_set_timing(int level);
 
 /* Profile of this thread's last mih_knn / mih_rnear / linscan_knn call. */
 MIH_API mih_status mih_last_profile(mih_profile *out);
+
+/* ------------------------------------------------------------------------
+ * mih_measure_ceilings -- throughput ceilings of the current GPU that the
+ * kernels' rooflines are quoted against (not part of the paper).  Each figure
+ * is one timed launch (after an untimed one) that keeps independent chains of
+ * the operation in flight on every SM:
+ *   popc_per_s              32-bit population counts per second (the linear
+ *                           scan computes the distance of Sec. 6 with them);
+ *   b1_mma_pairs128_per_s   (row, column) pairs of 128-bit operands per second
+ *                           of mma.sync m16n8k128 b1 AND-popcount, from which
+ *                           popc(a xor b) = popc a + popc b - 2 popc(a and b);
+ *   fp8_mma_tflops          mma.sync m16n8k32 e4m3 -> f32, and the pairs of
+ *                           128 +-1 elements per second it gives (Hamming
+ *                           distance = (q - <a, b>) / 2, exact in f32);
+ *   gather32_gbs            bytes per second of reads of random 32-byte
+ *                           sectors of a buffer of gather_bytes (at least
+ *                           64 MiB; use one far larger than L2).
+ * Synchronises `stream`.  Errors: MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA. */
+typedef struct {
+    double popc_per_s;
+    double b1_mma_pairs128_per_s;
+    double fp8_mma_tflops;
+    double fp8_mma_pairs128_per_s;
+    double gather32_gbs;
+    int32_t sms;
+    double sm_clock_mhz;   /* the device's maximum SM clock */
+} mih_ceilings;
+
+MIH_API mih_status mih_measure_ceilings(mih_ceilings *out, uint64_t gather_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
  * mih_set_wait_limit -- bounded device waits (not part of the paper).

@@ -33,7 +33,7 @@ EXPORTS = (
     "mih_substring_layout", "mih_cost_model", "mih_suggest_m", "mih_status_str",
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
     "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation", "mih_set_wait_limit",
-    "mih_cost_layout", "mih_autotune_layout",
+    "mih_cost_layout", "mih_autotune_layout", "mih_merge_topk", "mih_measure_ceilings",
 )
 
 
@@ -60,7 +60,7 @@ class mih_stats(ctypes.Structure):
 
 
 # mih_profile.kernel_ms / kernel_launches index (MIH_PROF_* in include/mih.h)
-PROF_KINDS = ("chunk", "slice", "probe", "plan", "stop", "select", "resolve", "scan")
+PROF_KINDS = ("chunk", "slice", "probe", "plan", "stop", "select", "scan")
 
 
 class mih_profile(ctypes.Structure):
@@ -75,6 +75,15 @@ class mih_profile(ctypes.Structure):
         d["kernel_ms"] = {k: float(v) for k, v in zip(PROF_KINDS, self.kernel_ms)}
         d["kernel_launches"] = {k: int(v) for k, v in zip(PROF_KINDS, self.kernel_launches)}
         return d
+
+
+class mih_ceilings(ctypes.Structure):
+    _fields_ = [("popc_per_s", ctypes.c_double), ("b1_mma_pairs128_per_s", ctypes.c_double),
+                ("fp8_mma_tflops", ctypes.c_double), ("fp8_mma_pairs128_per_s", ctypes.c_double),
+                ("gather32_gbs", ctypes.c_double), ("sms", ctypes.c_int32), ("sm_clock_mhz", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: (int(getattr(self, f)) if f == "sms" else float(getattr(self, f))) for f, _ in self._fields_}
 
 
 class mih_index_info(ctypes.Structure):
@@ -121,6 +130,10 @@ def load():
     lib.mih_cost_layout.restype = ctypes.c_double
     lib.mih_autotune_layout.argtypes = [P, u64, i32, P, u32, u32, i32, P, P, P, P]
     lib.mih_autotune_layout.restype = st
+    lib.mih_measure_ceilings.argtypes = [P, u64, P]
+    lib.mih_measure_ceilings.restype = st
+    lib.mih_merge_topk.argtypes = [P, P, u32, u32, u32, P, u32, P, P, P]
+    lib.mih_merge_topk.restype = st
     lib.mih_suggest_m.argtypes = [i32, u64]
     lib.mih_suggest_m.restype = i32
     lib.mih_status_str.argtypes = [st]
@@ -202,6 +215,13 @@ def mih_set_wait_limit(limit_us: int = 0, expire_first_wait: bool = False):
     """Limit of the bounded device waits of this thread's calls (0 = 1 s); with
     expire_first_wait the slice kernel's first waits run out (timeout test)."""
     _check(load().mih_set_wait_limit(limit_us, 1 if expire_first_wait else 0), "mih_set_wait_limit")
+
+
+def mih_measure_ceilings(gather_bytes: int = 8 << 30, stream=None) -> dict:
+    """Measured POPC, b1/fp8 mma.sync and random 32-byte gather rates of this GPU."""
+    c = mih_ceilings()
+    _check(load().mih_measure_ceilings(ctypes.byref(c), gather_bytes, _stream(stream)), "mih_measure_ceilings")
+    return c.as_dict()
 
 
 def mih_last_profile() -> dict:
@@ -441,6 +461,30 @@ def linscan_knn(codes, q: int, queries, k, stream=None, out=None):
     if off is not None:
         res["offsets"] = off
     return res
+
+
+def mih_merge_topk(ids, dist, id_base, k: int, stream=None, out=None):
+    """Exact k-NN of a database split into id ranges: ids/dist are (parts, nq,
+    k_in) CUDA int32 tensors of the parts' answers (ids relative to each part),
+    id_base the parts' first global ids.  Returns {"ids", "dist"} (nq, k)."""
+    import torch
+
+    if not (ids.is_cuda and dist.is_cuda):
+        raise ValueError("ids and dist must be CUDA tensors")
+    if ids.dim() != 3 or ids.shape != dist.shape or not (ids.is_contiguous() and dist.is_contiguous()):
+        raise ValueError("ids and dist must be contiguous (parts, nq, k_in) tensors")
+    parts, nq, k_in = ids.shape
+    base = np.ascontiguousarray(id_base, dtype=np.uint32)
+    if base.shape != (parts,):
+        raise ValueError("id_base must hold one entry per part")
+    if out is None:
+        oi = torch.empty((nq, k), dtype=torch.int32, device=ids.device)
+        od = torch.empty((nq, k), dtype=torch.int32, device=ids.device)
+    else:
+        oi, od = out
+    _check(load().mih_merge_topk(_ptr(ids), _ptr(dist), parts, nq, k_in, base.ctypes.data, k, _ptr(oi), _ptr(od),
+                                 _stream(stream)), "mih_merge_topk")
+    return {"ids": oi, "dist": od}
 
 
 def linscan_knn_noalloc(codes, q: int, queries, k: int, stream=None, out=None):

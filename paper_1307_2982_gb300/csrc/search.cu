@@ -318,8 +318,9 @@ __device__ __forceinline__ void store_batch(const SearchArgs& a, uint32_t q, int
         if (!((take_mask >> b) & 1u)) continue;
         if constexpr (MODE == kModeKnn) {
             // With inline codes the entry keeps the table position and the
-            // table (j + 1 in bits 41..49); resolve_ids_kernel turns it into
-            // the id after the search, off this kernel's critical path.
+            // table (j + 1 in bits 41..49); the selection turns the entries
+            // within d_k into ids after the search, off this kernel's
+            // critical path.
             const uint32_t p = base + before[b];
             const uint64_t e = lazy_id ? (static_cast<uint64_t>(j + 1) << kQueryShift) | pack_entry(dist[b], pos[b])
                                        : pack_entry(dist[b], id[b]);
@@ -413,29 +414,6 @@ __device__ __forceinline__ void process_records(const SearchArgs& a, uint32_t* w
         }
     }
     store_batch<MODE, B>(a, q, j, true, ids, pos, pos, dist, take_mask);
-}
-
-// Table positions stored by the k-NN search (inline codes) become ids: an
-// entry with a nonzero table tag t in bits 41..49 holds position p of table
-// t - 1, whose id is tables[t - 1].ids[p].  Only buffers that did not
-// overflow are read later, and of those only entries within d_k (the
-// selection reads no others), so only those are resolved.
-__global__ void resolve_ids_kernel(uint64_t* __restrict__ buf, const uint32_t* __restrict__ cnt, uint32_t cap,
-                                   uint32_t nq, const TableDesc* __restrict__ tables,
-                                   const int32_t* __restrict__ dk) {
-    for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
-        const uint32_t c = cnt[q];
-        if (c > cap) continue;
-        const uint32_t dmax = static_cast<uint32_t>(dk[q]);
-        uint64_t* e = buf + static_cast<uint64_t>(q) * cap;
-        for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) {
-            const uint64_t v = e[i];
-            const uint32_t tag = static_cast<uint32_t>(v >> kQueryShift);
-            const uint32_t d = static_cast<uint32_t>(v >> 32) & 0x1FFu;
-            if (tag != 0 && d <= dmax)
-                e[i] = (v & (0x1FFull << 32)) | __ldg(tables[tag - 1].ids + static_cast<uint32_t>(v));
-        }
-    }
 }
 
 // Add the warp's histogram to query q's global histogram and clear it.
@@ -538,11 +516,18 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
         if (lane == 0) c = atomicAdd(a.chunk_next, 1ull);
         c = __shfl_sync(0xFFFFFFFFu, c, 0);
         if (c >= total_chunks) break;
-        // query owning chunk c: last q with chunk_off[q] <= c
+        // query owning chunk c: the last q with chunk_off[q] <= c, by a 32-ary
+        // search (every lane probes one point per round; chunk_off[lo] <= c <
+        // chunk_off[hi] throughout)
         uint32_t lo = 0, hi = a.nq;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (__ldg(a.chunk_off + mid) <= c) lo = mid; else hi = mid;
+        for (;;) {
+            const uint32_t step = hi - lo > 32 ? (hi - lo + 31) / 32 : 1;
+            const uint32_t probe = lo + lane * step;
+            const bool le = probe < hi && __ldg(a.chunk_off + probe) <= c;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, le);   // lane 0 always (probe = lo)
+            lo += (31u - static_cast<uint32_t>(__clz(bal))) * step;
+            if (step == 1) break;
+            hi = min(hi, lo + step);
         }
         const uint32_t q = lo;
         uint64_t lc = c - __ldg(a.chunk_off + q);
@@ -1328,6 +1313,57 @@ __global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(const TableDesc
     if (threadIdx.x == kPlanThreads - 1) chunk_off[nq] = s_warp[kPlanThreads / 32 - 1];
 }
 
+// The same planning from per-query chunk counts that the stopping test wrote
+// for this wave: an exclusive scan of `counts` into chunk_off[0..nq], in
+// tiles of four counts per thread (coalesced loads), and the zeroed work
+// counters.  One CTA.
+__global__ void __launch_bounds__(kPlanThreads) plan_counts_kernel(const uint32_t* __restrict__ counts, uint32_t nq,
+                                                                   uint64_t* __restrict__ chunk_off,
+                                                                   unsigned long long* __restrict__ counters) {
+    __shared__ unsigned long long s_warp[kPlanThreads / 32];
+    __shared__ unsigned long long s_carry;
+    if (threadIdx.x < 2) counters[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_carry = 0ull;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    constexpr uint32_t kTile = 4u * kPlanThreads;
+    for (uint32_t base = 0; base < nq; base += kTile) {
+        const uint32_t i0 = base + 4u * threadIdx.x;
+        uint32_t c[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) c[r] = i0 + r < nq ? __ldg(counts + i0 + r) : 0u;
+        const unsigned long long sum = static_cast<unsigned long long>(c[0]) + c[1] + c[2] + c[3];
+        unsigned long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (static_cast<int>(lane) >= o) incl += v;
+        }
+        __syncthreads();   // the previous tile is done with s_warp and s_carry
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (static_cast<int>(lane) >= o) w += v;
+            }
+            s_warp[lane] = w;   // inclusive over warps
+        }
+        __syncthreads();
+        unsigned long long run = s_carry + (warp > 0 ? s_warp[warp - 1] : 0ull) + incl - sum;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (i0 + r < nq) chunk_off[i0 + r] = run;
+            run += c[r];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += s_warp[kPlanThreads / 32 - 1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) chunk_off[nq] = s_carry;
+}
+
 // Lookups of steps t0..t1 (sum of ring sizes, Eq. 1 per table).
 __device__ __forceinline__ uint64_t steps_lookups(const int* s_len, int m, int t0, int t1) {
     uint64_t l = 0;
@@ -1352,7 +1388,7 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
                                 int32_t* __restrict__ hist_done, uint32_t* __restrict__ cnt1, uint32_t cap,
                                 unsigned long long* __restrict__ qstats, unsigned int* __restrict__ active,
                                 const TableDesc* __restrict__ tables, int m, uint8_t* __restrict__ exh,
-                                long long scan_budget) {
+                                long long scan_budget, uint32_t* __restrict__ next_chunks) {
     __shared__ int s_len[kMaxTables];
     for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
     __syncthreads();
@@ -1388,6 +1424,7 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
             t_lo[q] = t + 1;
             qstats[4ull * q + 3] = static_cast<unsigned long long>(t);
             if (bound[q] < 0) cnt1[q] = cap + 1;  // nothing stored yet: second pass collects
+            next_chunks[q] = 0u;
         } else {
             hist_done[q] = t;
             if (bound[q] < 0 && first_reach >= 0) {
@@ -1404,6 +1441,8 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
             if (scan_budget >= 0 &&
                 qstats[4ull * q] + steps_lookups(s_len, m, t + 1, t + 1) > static_cast<unsigned long long>(scan_budget))
                 exh[q] = 1;
+            // chunks of the next wave's steps, for its planning
+            next_chunks[q] = static_cast<uint32_t>(query_chunks(s_len, m, n, t_lo, t_hi, exh, q));
             atomicAdd(active, 1u);
         }
     }
@@ -1438,11 +1477,40 @@ struct SelectArgs {
     uint32_t* out_ids;
     int32_t* out_dist;
     int* err;
+    const TableDesc* tables;   // lazy ids: an entry tagged t in bits 41..49 holds a position of table t - 1
+    uint32_t smem_entries;     // shared-memory slots of the launch (a power of two >= min(kmax, n))
 };
 
-// Top-min(k, n) of one query: every entry closer than d_k, then the
-// (k - #closer) smallest ids at distance d_k (radix select on the id), sorted
-// by (distance, id) with a bitonic network in shared memory.
+// Id of a stored entry (distance << 32 | id, or a tagged table position).
+__device__ __forceinline__ uint64_t resolved_entry(uint64_t e, const TableDesc* tables) {
+    const uint32_t tag = static_cast<uint32_t>(e >> kQueryShift);
+    const uint64_t v = e & kEntryMask;
+    if (tag == 0 || tables == nullptr) return v;
+    return (v & (0x1FFull << 32)) | __ldg(tables[tag - 1].ids + static_cast<uint32_t>(v));
+}
+
+// In-place bitonic sort of res[0, S) ascending (S a power of two), one CTA.
+__device__ __forceinline__ void bitonic_sort_smem(uint64_t* res, uint32_t S) {
+    for (uint32_t size = 2; size <= S; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < S / 2; i += blockDim.x) {
+                const uint32_t lo = 2 * i - (i & (stride - 1));
+                const uint32_t hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t x = res[lo], y = res[hi];
+                if ((x > y) == up) { res[lo] = y; res[hi] = x; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Top-min(k, n) of one query.  The histogram gives the number of entries
+// within d_k (below + ties).  When they fit in shared memory (the usual case)
+// one pass gathers them, with ids resolved, and a bitonic sort by (distance,
+// id) orders them.  Otherwise ids are resolved in place, every entry closer
+// than d_k is kept and the (k - #closer) smallest ids at d_k are found by a
+// radix select on the id, then sorted the same way.
 __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
     extern __shared__ uint64_t res[];
     __shared__ unsigned int s_n, s_hist[256];
@@ -1471,13 +1539,59 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
     const uint32_t quota = kk - static_cast<uint32_t>(s_below);
     const uint64_t* src;
     uint64_t nsrc;
+    // Tagged table positions exist only in the bounded buffer of the k-NN
+    // waves; the second-pass buffer holds ids already (its upper bits carry
+    // the query index, not a table).
+    const TableDesc* tables = nullptr;
     const uint32_t c1 = a.cnt1 ? a.cnt1[q] : 0xFFFFFFFFu;
     if (a.cnt1 && c1 <= a.cap) {
         src = a.buf1 + static_cast<uint64_t>(q) * a.cap;
         nsrc = c1;
+        tables = a.tables;
     } else {
         src = a.buf2 + a.base2[q];
         nsrc = s_below + ties;
+    }
+    const uint64_t within = s_below + ties;
+    if (within <= a.smem_entries) {
+        // one pass: the entries within d_k, ids resolved, into shared memory
+        for (uint64_t i = threadIdx.x; i < nsrc; i += blockDim.x) {
+            const uint64_t e = src[i];
+            if (static_cast<int>((e & kEntryMask) >> 32) <= dk) {
+                const unsigned int slot = atomicAdd(&s_n, 1u);
+                if (slot < within) res[slot] = resolved_entry(e, tables);
+            }
+        }
+        __syncthreads();
+        if (s_n != within) {
+            if (threadIdx.x == 0) atomicExch(a.err, 1);
+            return;
+        }
+        uint32_t S = 1;
+        while (S < within) S <<= 1;
+        for (uint32_t i = static_cast<uint32_t>(within) + threadIdx.x; i < S; i += blockDim.x) res[i] = ~0ull;
+        __syncthreads();
+        bitonic_sort_smem(res, S);
+        for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+            if (i < kk) {
+                oid[i] = static_cast<uint32_t>(res[i]);
+                odist[i] = static_cast<int32_t>(res[i] >> 32);
+            } else {
+                oid[i] = kPadId;
+                odist[i] = -1;
+            }
+        }
+        return;
+    }
+    if (tables) {
+        // large tie sets: ids of the entries within d_k resolved in place
+        uint64_t* w = const_cast<uint64_t*>(src);
+        for (uint64_t i = threadIdx.x; i < nsrc; i += blockDim.x) {
+            const uint64_t e = w[i];
+            if ((e >> kQueryShift) != 0 && static_cast<int>((e & kEntryMask) >> 32) <= dk)
+                w[i] = resolved_entry(e, tables);
+        }
+        __syncthreads();
     }
     const bool take_all_ties = quota >= ties;
     uint32_t P = 1;
@@ -1532,18 +1646,7 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
     }
     for (uint32_t i = kk + threadIdx.x; i < P; i += blockDim.x) res[i] = ~0ull;
     __syncthreads();
-    for (uint32_t size = 2; size <= P; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
-                const uint32_t lo = 2 * i - (i & (stride - 1));
-                const uint32_t hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const uint64_t x = res[lo], y = res[hi];
-                if ((x > y) == up) { res[lo] = y; res[hi] = x; }
-            }
-            __syncthreads();
-        }
-    }
+    bitonic_sort_smem(res, P);
     for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
         if (i < kk) {
             oid[i] = static_cast<uint32_t>(res[i]);
@@ -1584,13 +1687,14 @@ __global__ void phase2_plan_kernel(uint32_t nq, int qbits, const uint32_t* __res
 }
 
 __global__ void init_knn_kernel(uint32_t nq, uint64_t n, int32_t* t_lo, int32_t* t_hi, int32_t* bound,
-                                int32_t* dk, int32_t* hist_done) {
+                                int32_t* dk, int32_t* hist_done, uint32_t* chunks) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
         t_lo[q] = 0;
         t_hi[q] = n > 0 ? 0 : -1;
         bound[q] = -1;
         dk[q] = 0;
         hist_done[q] = -1;
+        chunks[q] = n > 0 ? 1u : 0u;   // step 0: ring 0 of table 0, one key
     }
 }
 
@@ -1856,12 +1960,15 @@ mih_status check_timeout(const Plan& p, cudaStream_t s) {
 // workspace's stream.
 template <int MODE>
 mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
-                    const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr) {
+                    const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr, const uint32_t* counts = nullptr) {
     const bool in_graph = cs != nullptr;
     cudaStream_t s = in_graph ? cs : ws.stream();
     {
         KernelSpan plan_span(s, MIH_PROF_PLAN, !in_graph);
-        if (static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
+        if (counts && static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
+            plan_counts_kernel<<<1, kPlanThreads, 0, s>>>(counts, a.nq, p.chunk_off, p.counters);
+            MIH_LAUNCH_CHECK();
+        } else if (static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
             plan_scan_kernel<<<1, kPlanThreads, 0, s>>>(ix->dev_tables, ix->m, a.nq, ix->n, t_lo, t_hi, a.exh,
                                                         p.chunk_off, p.counters);
             MIH_LAUNCH_CHECK();
@@ -2063,17 +2170,18 @@ mih_status check_k_args(uint32_t nq, const uint32_t* k, uint32_t k_uniform, cons
     return MIH_OK;
 }
 
-mih_status launch_select(const SelectInputs& in, Workspace& ws) {
-    if (in.nq == 0) return MIH_OK;
+// Shared-memory slots of a selection launch: room for min(kmax, n) results
+// and for the usual number of entries within d_k (one-pass selection).
+constexpr uint32_t kSelectSmemEntries = 4096;
+
+uint32_t select_slots(const SelectInputs& in) {
     uint32_t P = 1;
     const uint64_t kk_max = std::min<uint64_t>(in.kmax, in.n);
     while (P < kk_max) P <<= 1;
-    const size_t smem = static_cast<size_t>(P) * sizeof(uint64_t);
-    if (smem > 48 * 1024) MIH_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        static_cast<int>(smem)));
-    int* err;
-    MIH_TRY(ws.alloc(&err, 1));
-    MIH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ws.stream()));
+    return P > kSelectSmemEntries ? P : kSelectSmemEntries;
+}
+
+SelectArgs select_args(const SelectInputs& in, int* err, uint32_t slots) {
     SelectArgs a;
     a.nq = in.nq;
     a.n = in.n;
@@ -2091,6 +2199,21 @@ mih_status launch_select(const SelectInputs& in, Workspace& ws) {
     a.out_ids = in.out_ids;
     a.out_dist = in.out_dist;
     a.err = err;
+    a.tables = in.tables;
+    a.smem_entries = slots;
+    return a;
+}
+
+mih_status launch_select(const SelectInputs& in, Workspace& ws) {
+    if (in.nq == 0) return MIH_OK;
+    const uint32_t slots = select_slots(in);
+    const size_t smem = static_cast<size_t>(slots) * sizeof(uint64_t);
+    if (smem > 48 * 1024) MIH_CUDA(cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        static_cast<int>(smem)));
+    int* err;
+    MIH_TRY(ws.alloc(&err, 1));
+    MIH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), ws.stream()));
+    const SelectArgs a = select_args(in, err, slots);
     {
         KernelSpan ks(ws.stream(), MIH_PROF_SELECT);
         select_kernel<<<in.nq, 256, smem, ws.stream()>>>(a);
@@ -2107,34 +2230,16 @@ mih_status launch_select(const SelectInputs& in, Workspace& ws) {
 }
 
 // Selection with a caller-provided error flag (zeroed by the caller); no
-// allocation.  Only for min(kmax, n) <= 6144 (48 KB of shared memory).
+// allocation.  Only while the launch needs at most 48 KB of shared memory.
 mih_status launch_select_noalloc(const SelectInputs& in, int* err, cudaStream_t s) {
     if (in.nq == 0) return MIH_OK;
-    uint32_t P = 1;
-    const uint64_t kk_max = std::min<uint64_t>(in.kmax, in.n);
-    while (P < kk_max) P <<= 1;
-    const size_t smem = static_cast<size_t>(P) * sizeof(uint64_t);
+    const uint32_t slots = select_slots(in);
+    const size_t smem = static_cast<size_t>(slots) * sizeof(uint64_t);
     if (smem > 48 * 1024) {
         set_error("select: k too large for the fixed-scratch path");
         return MIH_EINVAL;
     }
-    SelectArgs a;
-    a.nq = in.nq;
-    a.n = in.n;
-    a.q = in.q;
-    a.kq = in.kq;
-    a.k_uniform = in.k_uniform;
-    a.out_off = in.out_off;
-    a.hist = in.hist;
-    a.dk = in.dk;
-    a.buf1 = in.buf1;
-    a.cap = in.cap;
-    a.cnt1 = in.cnt1;
-    a.buf2 = in.buf2;
-    a.base2 = in.base2;
-    a.out_ids = in.out_ids;
-    a.out_dist = in.out_dist;
-    a.err = err;
+    const SelectArgs a = select_args(in, err, slots);
     select_kernel<<<in.nq, 256, smem, s>>>(a);
     MIH_LAUNCH_CHECK();
     return MIH_OK;
@@ -2201,7 +2306,9 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_CUDA(cudaMemsetAsync(qstats, 0, sizeof(unsigned long long) * 4 * nq, s));
     int32_t* hist_done;
     MIH_TRY(ws.alloc(&hist_done, nq));
-    init_knn_kernel<<<grid1(nq), 256, 0, s>>>(nq, ix->n, t_lo, t_hi, bound, dk, hist_done);
+    uint32_t* wave_chunks;   // chunks of each query's steps in the next wave (written by the stopping test)
+    MIH_TRY(ws.alloc(&wave_chunks, nq));
+    init_knn_kernel<<<grid1(nq), 256, 0, s>>>(nq, ix->n, t_lo, t_hi, bound, dk, hist_done, wave_chunks);
     MIH_LAUNCH_CHECK();
     if (ix->n > 0 && query_stats == nullptr && ix->probe > 0) {
         // (with per-query counters requested the steps run exactly as Alg. 3
@@ -2246,12 +2353,12 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     // stopping test advances or retires it.  cs = capture stream (graph) or 0.
     auto wave = [&](cudaStream_t cs) -> mih_status {
         cudaStream_t ws_s = cs ? cs : s;
-        MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs));
+        MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs, wave_chunks));
         MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), ws_s));
         KernelSpan ks(ws_s, MIH_PROF_STOP, cs == nullptr);
         knn_stop_kernel<<<grid1(32ull * nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
                                                     hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
-                                                    exh, budget);
+                                                    exh, budget, wave_chunks);
         MIH_LAUNCH_CHECK();
         return MIH_OK;
     };
@@ -2339,13 +2446,6 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         MIH_TRY(check_timeout(plan, s));
         MIH_TRY(check_flag(err, "mih_knn: second pass found more codes within d_k than counted", s));
     }
-    if (ix->inline_codes && ix->n > 0) {
-        const unsigned blocks = nq < static_cast<uint32_t>(dev.sms) * 16u ? nq : static_cast<unsigned>(dev.sms) * 16u;
-        KernelSpan ks(s, MIH_PROF_RESOLVE);
-        resolve_ids_kernel<<<blocks, 256, 0, s>>>(buf1, cnt1, cap, nq, ix->dev_tables, dk);
-        MIH_LAUNCH_CHECK();
-    }
-
     SelectInputs si;
     si.nq = nq;
     si.n = ix->n;
@@ -2363,6 +2463,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     si.base2 = need;
     si.out_ids = out_ids;
     si.out_dist = out_dist;
+    si.tables = ix->inline_codes ? ix->dev_tables : nullptr;   // entries hold table positions
     MIH_TRY(launch_select(si, ws));
 
     if (query_stats)

@@ -9,6 +9,8 @@
 
 namespace mih {
 
+struct TableDesc;
+
 // Per-query inputs of the selection kernel.  For query q the candidate
 // entries (distance << 32 | id) are buf1[q*cap, q*cap + cnt1[q]) when
 // cnt1[q] <= cap, else buf2[base2[q], ...) holding exactly the codes within
@@ -30,12 +32,14 @@ struct SelectInputs {
     const uint64_t* base2;
     uint32_t* out_ids;
     int32_t* out_dist;
+    const TableDesc* tables = nullptr;   // device; set when entries may hold tagged table positions
 };
 
 mih_status launch_select(const SelectInputs& in, Workspace& ws);
 
 // The same selection writing a failure into `err` (device int, zeroed by the
-// caller) instead of allocating a flag; for min(kmax, n) <= 6144.
+// caller) instead of allocating a flag; for min(kmax, n) <= 4096 (32 KB of
+// shared memory).
 mih_status launch_select_noalloc(const SelectInputs& in, int* err, cudaStream_t s);
 
 // Validate k (uniform or per query, device) and the output pointers; *kmax

@@ -1,9 +1,15 @@
-"""Replicas: one process per GPU, each holding the whole database and index.
+"""Several GPUs, one process each.
 
-Queries are independent, so a batch is split into contiguous shards, one per
-rank, with no collective on the data path.  The only communication is
-host-level bookkeeping: the slowest rank's time (the job's time) and, when a
-caller wants every answer on one rank, a gather of the shards' results.
+Replicas: every rank holds the whole database and index and answers its own
+contiguous shard of the queries, with no collective on the data path; the
+only communication is host-level bookkeeping (the slowest rank's time, and a
+gather of the shards' results when a caller wants them on one rank).
+
+Database shards: every rank holds one contiguous id range of the database
+and its index, and answers every query over its range.  The exchange step is
+one all-gather of the ranks' (nq, k) answers; mih_merge_topk (a library
+kernel) then merges them exactly, since the ranges partition the database
+and (distance, id) is a total order.
 """
 from __future__ import annotations
 
@@ -45,3 +51,38 @@ def gather_rows(local, n_total: int, device=None):
     parts = [torch.zeros_like(pad) for _ in range(world)]
     dist.all_gather(parts, pad)
     return torch.cat([p[:s] for p, s in zip(parts, sizes)])
+
+
+def db_shard(n: int, world: int, rank: int):
+    """Contiguous id range [lo, hi) of an n-code database held by `rank`."""
+    return shard(n, world, rank)
+
+
+def all_gather_parts(ids, dist):
+    """Every rank's (nq, k) answers stacked in rank order: (world, nq, k) each."""
+    import torch
+    import torch.distributed as dist_
+
+    if not (dist_.is_available() and dist_.is_initialized()) or dist_.get_world_size() == 1:
+        return ids.unsqueeze(0).contiguous(), dist.unsqueeze(0).contiguous()
+    world = dist_.get_world_size()
+    pi = [torch.empty_like(ids) for _ in range(world)]
+    pd = [torch.empty_like(dist) for _ in range(world)]
+    dist_.all_gather(pi, ids.contiguous())
+    dist_.all_gather(pd, dist.contiguous())
+    return torch.stack(pi).contiguous(), torch.stack(pd).contiguous()
+
+
+def knn_db_sharded(index, queries, k: int, n_total: int, stream=None):
+    """Exact k-NN over the whole database from this rank's id range: the
+    rank's own mih_knn, the all-gather of every rank's answer and the exact
+    merge (mih_merge_topk).  Every rank returns the same {"ids", "dist"}."""
+    import torch.distributed as dist_
+
+    from . import mih_knn, mih_merge_topk
+
+    world = dist_.get_world_size() if (dist_.is_available() and dist_.is_initialized()) else 1
+    local = mih_knn(index, queries, k, stream=stream)
+    pi, pd = all_gather_parts(local["ids"], local["dist"])
+    bases = [db_shard(n_total, world, r)[0] for r in range(world)]
+    return mih_merge_topk(pi, pd, bases, k, stream=stream)

@@ -461,6 +461,48 @@ def test_autotune_layout(gpu_lib, orc):
     assert np.array_equal(ids_of(r["ids"]), want_ids) and np.array_equal(host(r["dist"]), want_dist)
 
 
+@pytest.mark.parametrize("q,m,sizes,k", [(128, 4, [40_000, 25_001, 35_000], 100), (64, 3, [30_000, 70, 20_000], 100),
+                                         (256, 9, [500, 300, 400], 2000)])
+def test_db_shards_merge_to_the_whole_answer(gpu_lib, orc, q, m, sizes, k):
+    """A database split into id ranges, one index per range, answers merged by
+    mih_merge_topk: equal to the oracle over the whole database (Sec. 1.1).
+    Covers a range with fewer than k codes and k above the whole database."""
+    import torch
+
+    mih = gpu_lib
+    n = sum(sizes)
+    db, qs = workload("lsh", q, n, 77, seed=81)
+    codes, queries = to_dev(db), to_dev(qs)
+    bases = list(np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64))
+    ids, dist = [], []
+    for lo, sz in zip(bases, sizes):
+        ix = mih.mih_build(codes[lo:lo + sz].contiguous(), q, m)
+        r = mih.mih_knn(ix, queries, k)
+        ids.append(r["ids"])
+        dist.append(r["dist"])
+        ix.free()
+    got = mih.mih_merge_topk(torch.stack(ids).contiguous(), torch.stack(dist).contiguous(), bases, k)
+    want_ids, want_dist = orc.knn(db, qs, k)
+    assert np.array_equal(ids_of(got["ids"]), want_ids)
+    assert np.array_equal(host(got["dist"]), want_dist)
+    # merging fewer results than each part holds
+    got5 = mih.mih_merge_topk(torch.stack(ids).contiguous(), torch.stack(dist).contiguous(), bases, 5)
+    w5, d5 = orc.knn(db, qs, 5)
+    assert np.array_equal(ids_of(got5["ids"]), w5) and np.array_equal(host(got5["dist"]), d5)
+
+
+def test_measured_ceilings_are_plausible(gpu_lib):
+    """The ceilings the rooflines are quoted against: positive, and within a
+    factor of the unit counts and clock (popc: at most 64 per SM and clock)."""
+    mih = gpu_lib
+    c = mih.mih_measure_ceilings(gather_bytes=1 << 30)
+    assert c["sms"] > 0 and c["sm_clock_mhz"] > 0
+    upper = 64.0 * c["sms"] * c["sm_clock_mhz"] * 1e6
+    assert 0 < c["popc_per_s"] <= upper * 1.05
+    assert c["b1_mma_pairs128_per_s"] > 0 and c["fp8_mma_tflops"] > 0 and c["gather32_gbs"] > 0
+    assert c["fp8_mma_pairs128_per_s"] == pytest.approx(c["fp8_mma_tflops"] * 1e12 / 256.0)
+
+
 def test_autotune_picks_a_candidate(gpu_lib, orc):
     """Sec. 6: m chosen by timing the search on hold-out queries."""
     mih = gpu_lib
