@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="use the workload's default m")
     ap.add_argument("--serve-qps", type=float, default=200_000.0, help="offered load of the serving check")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--tail-from", type=int, default=0,
+                    help="step from which k-NN queries run two steps per wave (0 = library default 2m, <0 never)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (1e9 x 64, 1e9 x 256, three-database serving) after the headline")
     ap.add_argument("--opt-substrings", action="store_true",
@@ -339,7 +341,8 @@ def run_ours(a):
     # index build (Algorithm 1), timed on the device
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
-    index = mih.mih_build(codes, q, m, probe=a.probe, executor=EXECUTORS[a.executor], bit_order=order)
+    index = mih.mih_build(codes, q, m, probe=a.probe, executor=EXECUTORS[a.executor], bit_order=order,
+                          tail_from=a.tail_from)
     ev1.record()
     torch.cuda.synchronize()
     build_ms = ev0.elapsed_time(ev1)
@@ -505,16 +508,46 @@ def run_ours(a):
                    "identical_to_mih": same, "pairs_per_s": pairs / (ls_ms / 1000.0),
                    "scan_kernel_ms": lprof["main_ms"]}
 
+    # ---- the other form of the scan on the first 1000 queries (fp8 tensor-core
+    # products; the timed pass above is the default form, xor + popcount)
+    if linscan:
+        pq = queries[:1000].contiguous()
+        pk = karg if kt is None else kt[:1000].contiguous()
+        mih.mih_set_scan_kernel(mih.MIH_SCAN_TENSOR)
+        mih.linscan_knn(codes, q, pq[:64], karg if kt is None else kt[:64].contiguous())
+        torch.cuda.synchronize()
+        g0.record()
+        pls = mih.linscan_knn(codes, q, pq, pk)
+        g1.record()
+        torch.cuda.synchronize()
+        mih.mih_set_scan_kernel(mih.MIH_SCAN_AUTO)
+        p_ms = g0.elapsed_time(g1)
+        nrow = pq.shape[0]
+        same_p = bool(torch.equal(pls["ids"], ls["ids"][:nrow]) and torch.equal(pls["dist"], ls["dist"][:nrow])) \
+            if kt is None else None
+        linscan["kernel"] = "xor + popcount with an OR lower bound"
+        linscan["tensor_form"] = {"kernel": "fp8 tensor-core products (mma.sync m16n8k32 e4m3, +-1 codes)",
+                                  "queries": nrow, "pairs_per_s": float(n) * nrow / (p_ms / 1000.0),
+                                  "ms": p_ms, "identical": same_p}
+
     # ---- measured ceilings of this GPU (POPC, tensor-core Hamming forms,
     # random 32-byte reads), after the timed regions
     ceilings = mih.mih_measure_ceilings(gather_bytes=8 << 30)
     if linscan:
-        # the scan's roofline: one POPC per pair (OR lower bound of G words,
-        # most pairs) against the measured POPC rate
+        # the tensor-core scan against the measured fp8 mma.sync rate (a pair
+        # of q-bit codes is q multiply-adds); the popcount form against the
+        # measured POPC rate at one POPC per pair (the OR lower bound settles
+        # most pairs in one)
+        fp8_pairs = ceilings["fp8_mma_tflops"] * 1e12 / (2.0 * q)
         linscan["roofline"] = {"bound": "alu", "achieved": linscan["pairs_per_s"], "unit": "pairs/s",
                                "peak": ceilings["popc_per_s"], "frac": linscan["pairs_per_s"] / ceilings["popc_per_s"],
                                "peak_source": "measured POPC rate (mih_measure_ceilings)",
                                "model": "one 32-bit POPC per (query, code) pair"}
+        tf = linscan["tensor_form"]
+        tf["roofline"] = {"bound": "tensor", "achieved": tf["pairs_per_s"], "unit": "pairs/s",
+                          "peak": fp8_pairs, "frac": tf["pairs_per_s"] / fp8_pairs,
+                          "peak_source": "measured fp8 mma.sync rate (mih_measure_ceilings)",
+                          "model": f"{q} e4m3 multiply-adds per (query, code) pair"}
 
     # ---- serving: Poisson k=100 requests against the resident index (p50/p99)
     serve = None
@@ -565,6 +598,7 @@ def run_ours(a):
                    "substring_bits": info["substring_length"], "table_kind": info["table_kind"],
                    "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s,
                    "inline_codes": info["inline_codes"], "executor": a.executor, "substrings": substrings,
+                   "tail_from": a.tail_from if a.tail_from else 2 * m,
                    "autotune": tune},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "mih_stats_per_step": {kk: v / a.steps for kk, v in stats_acc.items()},

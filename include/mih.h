@@ -89,7 +89,14 @@ typedef struct {
                               waves; MIH_EXEC_HOST = a host loop that reads the
                               number of active queries after every wave.
                               0 = MIH_EXEC_AUTO (the graph). */
-    int32_t pad_;          /* must be zero */
+    int32_t tail_from;     /* Step from which a k-NN query runs two Alg. 3 steps
+                              per wave instead of one (results unchanged: after
+                              steps 0..t every code within t bits is found,
+                              Prop. 2, so the stopping test after a wave stays
+                              exact; a query may do one step more than Alg. 3).
+                              Saves waves when few slow queries remain.  0 =
+                              default (step 2m), negative = never.  Never with
+                              per-query counters requested (they are Alg. 3's). */
     const int32_t *bit_order; /* Sec. 5.5 "Substring Optimization": NULL = the
                               consecutive substrings of Sec. 2.1.  Otherwise a
                               host array of q distinct bit indices, read during
@@ -211,6 +218,13 @@ MIH_API mih_status mih_knn(const mih_index *index, const uint64_t *queries, uint
                    uint32_t *out_ids, int32_t *out_dist, uint64_t *query_stats,
                    mih_stats *stats, void *stream);
 
+/* CSR offsets for per-query k (the out_offsets of mih_knn / linscan_knn),
+ * computed on the device: out_offsets[i] = k[0] + ... + k[i-1] for
+ * i = 0..nq, so out_offsets[nq] is the total.  k: device uint32[nq];
+ * out_offsets: device uint64[nq + 1].  Stream-ordered (does not synchronise).
+ * Errors: MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA. */
+MIH_API mih_status mih_k_offsets(const uint32_t *k, uint32_t nq, uint64_t *out_offsets, void *stream);
+
 /* ------------------------------------------------------------------------
  * mih_rnear -- Algorithm 2 (Sec. 2.2): all codes within r bits of each query.
  *
@@ -268,6 +282,20 @@ MIH_API mih_status linscan_knn(const uint64_t *codes, uint64_t n, int q, const u
 MIH_API mih_status mih_merge_topk(const uint32_t *ids, const int32_t *dist, uint32_t parts, uint32_t nq,
                                   uint32_t k_in, const uint32_t *id_base, uint32_t k, uint32_t *out_ids,
                                   int32_t *out_dist, void *stream);
+
+/* ------------------------------------------------------------------------
+ * mih_set_scan_kernel -- which kernel linscan_knn uses for calls from the
+ * calling host thread (results are identical):
+ *   MIH_SCAN_POPC    xor and population count per 32-bit word (Sec. 6
+ *                    "Hamming Distance"), with an OR lower bound that settles
+ *                    most pairs in one popcount;
+ *   MIH_SCAN_TENSOR  fp8 tensor-core products: bits as +-1 e4m3 values, so the
+ *                    dot product of two codes is q - 2 d (exact in f32);
+ *   MIH_SCAN_AUTO    the popcount form (measured faster on GB300 at 1e9 x
+ *                    128-bit codes and 10^4 queries).
+ * Errors: MIH_EINVAL for an unknown kind. */
+enum { MIH_SCAN_AUTO = 0, MIH_SCAN_POPC = 1, MIH_SCAN_TENSOR = 2 };
+MIH_API mih_status mih_set_scan_kernel(int kind);
 
 /* ------------------------------------------------------------------------
  * mih_autotune -- choose the number of substrings m by timing the search on

@@ -25,6 +25,7 @@ _lib = None
 MIH_OK, MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EOVERFLOW, MIH_ETIMEOUT, MIH_EINTERNAL = range(7)
 MIH_TABLE_AUTO, MIH_TABLE_DIRECT, MIH_TABLE_SPARSE = 0, 1, 2
 MIH_EXEC_AUTO, MIH_EXEC_HOST, MIH_EXEC_GRAPH = 0, 1, 2
+MIH_SCAN_AUTO, MIH_SCAN_POPC, MIH_SCAN_TENSOR = 0, 1, 2
 MIH_MAX_K = 8192
 PAD_ID = 0xFFFFFFFF
 
@@ -34,6 +35,7 @@ EXPORTS = (
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
     "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation", "mih_set_wait_limit",
     "mih_cost_layout", "mih_autotune_layout", "mih_merge_topk", "mih_measure_ceilings",
+    "mih_set_scan_kernel", "mih_k_offsets",
 )
 
 
@@ -46,7 +48,7 @@ class MihError(RuntimeError):
 class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
                 ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("executor", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("bit_order", ctypes.POINTER(ctypes.c_int32)),
+                ("tail_from", ctypes.c_int32), ("bit_order", ctypes.POINTER(ctypes.c_int32)),
                 ("substring_length", ctypes.POINTER(ctypes.c_int32)), ("reserved", ctypes.c_int32 * 6)]
 
 
@@ -130,6 +132,10 @@ def load():
     lib.mih_cost_layout.restype = ctypes.c_double
     lib.mih_autotune_layout.argtypes = [P, u64, i32, P, u32, u32, i32, P, P, P, P]
     lib.mih_autotune_layout.restype = st
+    lib.mih_k_offsets.argtypes = [P, u32, P, P]
+    lib.mih_k_offsets.restype = st
+    lib.mih_set_scan_kernel.argtypes = [i32]
+    lib.mih_set_scan_kernel.restype = st
     lib.mih_measure_ceilings.argtypes = [P, u64, P]
     lib.mih_measure_ceilings.restype = st
     lib.mih_merge_topk.argtypes = [P, P, u32, u32, u32, P, u32, P, P, P]
@@ -215,6 +221,11 @@ def mih_set_wait_limit(limit_us: int = 0, expire_first_wait: bool = False):
     """Limit of the bounded device waits of this thread's calls (0 = 1 s); with
     expire_first_wait the slice kernel's first waits run out (timeout test)."""
     _check(load().mih_set_wait_limit(limit_us, 1 if expire_first_wait else 0), "mih_set_wait_limit")
+
+
+def mih_set_scan_kernel(kind: int):
+    """linscan_knn's kernel for this thread: MIH_SCAN_AUTO, MIH_SCAN_POPC or MIH_SCAN_TENSOR."""
+    _check(load().mih_set_scan_kernel(int(kind)), "mih_set_scan_kernel")
 
 
 def mih_measure_ceilings(gather_bytes: int = 8 << 30, stream=None) -> dict:
@@ -319,7 +330,7 @@ class MihIndex:
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
               inline_codes: int = 0, probe: int = 0, executor: int = MIH_EXEC_AUTO, bit_order=None,
-              substring_length=None, stream=None) -> MihIndex:
+              substring_length=None, tail_from: int = 0, stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
@@ -327,6 +338,7 @@ def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_fact
     p.inline_codes = inline_codes
     p.probe = probe
     p.executor = executor
+    p.tail_from = tail_from
     if bit_order is not None:
         order = np.ascontiguousarray(bit_order, dtype=np.int32)
         if order.shape != (q,):
@@ -376,17 +388,35 @@ def mih_free(index: MihIndex):
     index.free()
 
 
-def _k_args(nq, k, device):
-    """Uniform int k or a per-query CUDA uint32/int32 tensor -> C arguments."""
+def _k_args(nq, k, device, stream=None):
+    """Uniform int k, or per-query k -> C arguments (k, k_uniform, offsets, output shape).
+
+    Host k (numpy array or CPU tensor): the CSR offsets and their total come
+    from the host values and both arrays are copied to the device, with no
+    device synchronisation.  Device k: the library computes the offsets
+    (mih_k_offsets) and the total is read back once, to size the outputs."""
     import torch
 
     if isinstance(k, int):
         return None, k, None, (nq, k)
-    kt = k if k.is_cuda else k.to(device)
-    kt = kt.to(torch.int32).contiguous()
-    off = torch.zeros(nq + 1, dtype=torch.int64, device=device)
-    off[1:] = torch.cumsum(kt.to(torch.int64), 0)
-    return kt, 0, off, (int(off[-1].item()),)
+    if isinstance(k, torch.Tensor) and k.is_cuda:
+        kt = k.to(torch.int32).contiguous()
+        off = torch.empty(nq + 1, dtype=torch.int64, device=device)
+        _check(load().mih_k_offsets(_ptr(kt), nq, _ptr(off), _stream(stream)), "mih_k_offsets")
+        return kt, 0, off, (int(off[-1].item()),)
+    if isinstance(k, torch.Tensor):
+        kc = k if (k.dtype == torch.int32 and k.is_contiguous()) else k.to(torch.int32).contiguous()
+        kh = kc.numpy()
+    else:
+        kh = np.ascontiguousarray(k, dtype=np.int32)
+        kc = torch.from_numpy(kh)
+    if kh.shape != (nq,):
+        raise ValueError("per-query k must hold one entry per query")
+    offh = np.zeros(nq + 1, dtype=np.int64)
+    np.cumsum(kh, dtype=np.int64, out=offh[1:])
+    kt = kc.to(device, non_blocking=True)
+    off = torch.from_numpy(offh).to(device)
+    return kt, 0, off, (int(offh[-1]),)
 
 
 def mih_knn(index: MihIndex, queries, k, stream=None, query_stats: bool = False, out=None):
@@ -394,7 +424,7 @@ def mih_knn(index: MihIndex, queries, k, stream=None, query_stats: bool = False,
     import torch
 
     qptr, nq = _codes_arg(queries, index.q)
-    kt, ku, off, shape = _k_args(nq, k, queries.device)
+    kt, ku, off, shape = _k_args(nq, k, queries.device, stream)
     if out is None:
         ids = torch.empty(shape, dtype=torch.int32, device=queries.device)
         dist = torch.empty(shape, dtype=torch.int32, device=queries.device)
@@ -449,7 +479,7 @@ def linscan_knn(codes, q: int, queries, k, stream=None, out=None):
 
     cptr, n = _codes_arg(codes, q)
     qptr, nq = _codes_arg(queries, q)
-    kt, ku, off, shape = _k_args(nq, k, queries.device)
+    kt, ku, off, shape = _k_args(nq, k, queries.device, stream)
     if out is None:
         ids = torch.empty(shape, dtype=torch.int32, device=queries.device)
         dist = torch.empty(shape, dtype=torch.int32, device=queries.device)

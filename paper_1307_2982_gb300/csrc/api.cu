@@ -85,6 +85,10 @@ KernelSpan::~KernelSpan() {
 
 // Limit of the bounded waits on bulk copies, and the timeout test switch
 // (mih_set_wait_limit), per host thread.
+// Linear-scan kernel form (mih_set_scan_kernel), per host thread.
+thread_local int g_scan_kernel = MIH_SCAN_AUTO;
+int scan_kernel_choice() { return g_scan_kernel; }
+
 thread_local uint64_t g_wait_ns = 1000000000ull;
 thread_local bool g_wait_test = false;
 uint64_t wait_limit_ns() { return g_wait_ns; }
@@ -306,6 +310,15 @@ const char* mih_status_str(mih_status s) {
 const char* mih_last_error(void) { return mih::g_err; }
 
 void mih_set_timing(int level) { mih::g_prof.timing = level < 0 ? 0 : (level > 2 ? 2 : level); }
+
+mih_status mih_set_scan_kernel(int kind) {
+    if (kind < MIH_SCAN_AUTO || kind > MIH_SCAN_TENSOR) {
+        mih::set_error("mih_set_scan_kernel: unknown kind %d", kind);
+        return MIH_EINVAL;
+    }
+    mih::g_scan_kernel = kind;
+    return MIH_OK;
+}
 
 mih_status mih_set_wait_limit(uint32_t limit_us, int expire_first_wait) {
     if (limit_us > 60u * 1000u * 1000u) {

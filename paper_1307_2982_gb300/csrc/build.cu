@@ -356,8 +356,8 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
         for (int i = 0; i < 6; ++i)
-            if (params->reserved[i] != 0 || params->pad_ != 0) {
-                set_error("mih_build: params.reserved and params.pad_ must be zero");
+            if (params->reserved[i] != 0) {
+                set_error("mih_build: params.reserved must be zero");
                 return MIH_EINVAL;
             }
         if (params->bit_order) MIH_TRY(check_bit_order(params->bit_order, q));
@@ -393,6 +393,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->scan_factor = params ? params->scan_factor : 0;
     ix->probe = (!params || params->probe == 0) ? 1024 : (params->probe < 0 ? 0 : params->probe);
     ix->executor = params ? params->executor : MIH_EXEC_AUTO;
+    ix->tail_from = (!params || params->tail_from == 0) ? 2 * m : (params->tail_from < 0 ? -1 : params->tail_from);
     if (params && params->bit_order) {
         // Optimised substrings (Sec. 5.5): the tables see codes whose bits are
         // permuted; the index keeps that copy and the order for the queries.

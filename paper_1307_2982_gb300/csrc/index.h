@@ -23,5 +23,6 @@ struct mih_index {
     bool inline_codes = false;                  // tables hold codes in bucket order
     int probe = 1024;                           // bound-probe entries per bucket (0 = off)
     int executor = 0;                           // MIH_EXEC_* for the k-NN wave loop
+    int tail_from = 0;                          // step from which queries run two steps per wave (-1: never)
     int32_t* bit_order = nullptr;               // device, q entries: optimised substrings (Sec. 5.5), or null
 };

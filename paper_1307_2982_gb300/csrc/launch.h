@@ -30,6 +30,9 @@ bool wait_test_expire();
 // Timing level of the calling thread (mih_set_timing).
 int timing_level();
 
+// Linear-scan kernel form chosen by the calling thread (MIH_SCAN_*).
+int scan_kernel_choice();
+
 // An event pair around one kernel launch of the given MIH_PROF_* kind, on
 // stream s, recorded only with per-kernel timing (level 2) inside a C-ABI
 // call and when `active` (false while the stream is being captured).

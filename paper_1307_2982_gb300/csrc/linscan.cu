@@ -179,6 +179,185 @@ __global__ void __launch_bounds__(kLsThreads) linscan_kernel(ScanArgs a) {
     }
 }
 
+// ------------------------------------------------------------ tensor-core form
+// The same scan with the distances from fp8 tensor-core products.  A code bit
+// b becomes the e4m3 value (-1)^b (0x38 = +1.0, 0xB8 = -1.0), so the dot
+// product of two q-bit codes is (#equal bits - #differing bits) = q - 2 d and
+// d = (q - <g, c>) / 2 (Sec. 6's distance, on the tensor pipe); every partial
+// sum is an integer of magnitude <= 256, exact in the f32 accumulators.  One
+// 32-bit code word is one K-step of mma.m16n8k32.
+//
+// A warp holds the A fragments of its 16 MT queries in registers for the whole
+// scan and streams 8 NT codes per step, building their B fragments from the
+// code words; the CTA's warps scan the same codes (L1 reuse) for different
+// queries.  A pair is kept when dot >= q - 2 thr_q, i.e. d <= thr_q; the warp
+// only looks at single pairs when one of its lanes has such a pair.
+constexpr int kMmaWarps = 4;
+
+template <int W>
+struct MmaShape {
+    static constexpr int MT = W == 4 ? 2 : 4;   // 16-query tiles per warp (A fragments in registers)
+    static constexpr int NT = 2;                // 8-code tiles per step
+};
+
+// Four code bits (bit i of `nibble`) -> four e4m3 bytes 0x38 | (bit_i << 7):
+// the multiplier puts bit i at bit 8 i + 7 (the copies of the nibble do not overlap).
+__device__ __forceinline__ uint32_t pm1_e4m3x4(uint32_t nibble) {
+    return ((nibble * 0x10204080u) & 0x80808080u) | 0x38383838u;
+}
+
+__device__ __forceinline__ void mma_e4m3(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int W>
+__global__ void __launch_bounds__(kMmaWarps * 32) linscan_mma_kernel(ScanArgs a) {
+    constexpr int KS = 2 * W;                       // K-steps: 32-bit words per code
+    constexpr int MT = MmaShape<W>::MT, NT = MmaShape<W>::NT;
+    constexpr int QW = 16 * MT, QC = QW * kMmaWarps, CT = 8 * NT;
+    constexpr int kRefreshSteps = kLsRefresh * kLsTile / CT;
+    __shared__ int s_thr[QC];
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = lane_id(), g = lane >> 2, t = lane & 3;
+    const uint32_t q0 = blockIdx.x * QC;
+    const uint32_t nql = min(static_cast<uint32_t>(QC), a.nq - q0);
+    for (int i = threadIdx.x; i < QC; i += blockDim.x) s_thr[i] = static_cast<uint32_t>(i) < nql ? a.thr[q0 + i] : -1;
+    __syncthreads();
+    // A fragments: rows g and g + 8 of each query tile; bits 4t..4t+3 of a
+    // word in registers 0/1, bits 16+4t..16+4t+3 in registers 2/3
+    uint32_t A[MT][KS][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t r = warp * QW + mt * 16 + g + 8 * h;
+            Code<W> v{};
+            if (r < nql) v = load_code<W>(a.queries, q0 + r);
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint32_t wd = static_cast<uint32_t>(v.w[ks >> 1] >> (32 * (ks & 1)));
+                A[mt][ks][h] = pm1_e4m3x4((wd >> (4 * t)) & 0xFu);
+                A[mt][ks][2 + h] = pm1_e4m3x4((wd >> (16 + 4 * t)) & 0xFu);
+            }
+        }
+    }
+    // Kept when dot >= cut = q - 2 thr (thr = -1: cut = q + 2, never).  The
+    // accumulators start at 0.5 - cut, so they end at dot - cut + 0.5: at
+    // least +0.5 for a kept pair, at most -0.5 otherwise (exact in f32, never
+    // zero), and the sign bit alone decides.
+    float cut[MT][2];
+    auto load_cuts = [&]() {
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                cut[mt][h] = static_cast<float>(a.qbits - 2 * s_thr[warp * QW + mt * 16 + g + 8 * h]);
+    };
+    load_cuts();
+    const uint64_t begin = static_cast<uint64_t>(blockIdx.y) * a.split_len;
+    const uint64_t end = min(a.n, begin + a.split_len);
+    // code words of the current step; the next step's are loaded before this
+    // step's products run
+    uint32_t cw[NT][KS];
+    auto load_step = [&](uint64_t base, uint32_t (&dst)[NT][KS]) {
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const uint64_t i = base + nt * 8 + g;
+            Code<W> v{};
+            if (i < end) v = load_code<W>(a.codes, i);
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) dst[nt][ks] = static_cast<uint32_t>(v.w[ks >> 1] >> (32 * (ks & 1)));
+        }
+    };
+    load_step(begin, cw);
+    int step_no = 0;
+    for (uint64_t base = begin; base < end; base += CT, ++step_no) {
+        uint32_t nx[NT][KS];
+        load_step(base + CT, nx);
+        float D[MT][NT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) D[mt][nt][e] = 0.5f - cut[mt][e >> 1];
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            uint32_t b0[NT], b1[NT];
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                b0[nt] = pm1_e4m3x4((cw[nt][ks] >> (4 * t)) & 0xFu);
+                b1[nt] = pm1_e4m3x4((cw[nt][ks] >> (16 + 4 * t)) & 0xFu);
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) mma_e4m3(D[mt][nt], A[mt][ks], b0[nt], b1[nt]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) cw[nt][ks] = nx[nt][ks];
+        // accumulator e: row g + 8 (e >> 1) of the query tile, code 2t + (e & 1)
+        // of the code tile; a clear sign bit in the AND of all of them means
+        // some pair of this lane is kept
+        uint32_t signs = 0xFFFFFFFFu;
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) signs &= __float_as_uint(D[mt][nt][e]);
+        if (__any_sync(0xFFFFFFFFu, (signs >> 31) == 0u)) {
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int h = e >> 1;
+                        const uint64_t i = base + nt * 8 + 2 * t + (e & 1);
+                        if (i >= end || (__float_as_uint(D[mt][nt][e]) >> 31) != 0u) continue;
+                        const int dot = __float2int_rn(D[mt][nt][e] - 0.5f + cut[mt][h]);
+                        const int d = (a.qbits - dot) >> 1;
+                        const uint32_t q = q0 + warp * QW + mt * 16 + g + 8 * h;
+                        const uint32_t id = static_cast<uint32_t>(i);
+                        const uint32_t p = atomicAdd(&a.cnt[q], 1u);
+                        if (!a.second_pass) {
+                            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, id);
+                            atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.qbits + 1) + d], 1u);
+                        } else {
+                            const uint64_t slot = a.base[q] + p;
+                            if (slot < a.base[q + 1]) a.buf[slot] = pack_entry(d, id);
+                            else atomicExch(a.err, 1);
+                        }
+                    }
+        }
+        if (!a.second_pass && (step_no % kRefreshSteps) == kRefreshSteps - 1) {
+            __syncthreads();
+            for (uint32_t r = threadIdx.x; r < nql; r += blockDim.x) {
+                const uint32_t q = q0 + r;
+                const uint32_t kk = kk_of(a.kq, a.k_uniform, q, a.n);
+                const uint32_t* h = a.hist + static_cast<uint64_t>(q) * (a.qbits + 1);
+                const int old = s_thr[r];
+                uint32_t cum = 0;
+                for (int d = 0; d < old; ++d) {
+                    cum += __ldcg(h + d);  // written by other CTAs' atomics: bypass L1
+                    if (cum >= kk) {
+                        s_thr[r] = d;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            load_cuts();
+        }
+    }
+}
+
 // Exact distance histogram of the first S codes per query (one warp per
 // query, lane-private columns in shared memory), then the bound: the smallest
 // D with at least min(k, n) sample codes within D bits (q if S < min(k, n)).
@@ -290,6 +469,37 @@ mih_status launch_scan(const ScanArgs& a, int W, int G, dim3 grid, cudaStream_t 
     return launch_scan_w<4>(a, G, grid, s);
 }
 
+// Grid of a scan: query tiles x CTA columns over the codes, enough columns to
+// fill the GPU about 4 times over; columns are whole multiples of kLsTile.
+struct ScanGrid {
+    dim3 grid;
+    uint64_t split_len;
+};
+
+ScanGrid scan_grid(uint64_t n, uint32_t nq, uint32_t queries_per_cta, int sms) {
+    const uint32_t qtiles = (nq + queries_per_cta - 1) / queries_per_cta;
+    const uint64_t target = static_cast<uint64_t>(sms) * 4;
+    uint64_t splits = (target + qtiles - 1) / qtiles;
+    const uint64_t max_splits = (n + kLsTile - 1) / kLsTile;
+    if (splits > max_splits) splits = max_splits;
+    if (splits < 1) splits = 1;
+    if (splits > 65535) splits = 65535;
+    uint64_t split_len = (n + splits - 1) / splits;
+    split_len = (split_len + kLsTile - 1) / kLsTile * kLsTile;
+    splits = (n + split_len - 1) / split_len;
+    return {dim3(qtiles, static_cast<unsigned>(splits)), split_len};
+}
+
+uint32_t mma_queries_per_cta(int W) { return (W == 4 ? 2u : 4u) * 16u * kMmaWarps; }
+
+mih_status launch_scan_mma(const ScanArgs& a, int W, dim3 grid, cudaStream_t s) {
+    if (W == 1) linscan_mma_kernel<1><<<grid, kMmaWarps * 32, 0, s>>>(a);
+    else if (W == 2) linscan_mma_kernel<2><<<grid, kMmaWarps * 32, 0, s>>>(a);
+    else linscan_mma_kernel<4><<<grid, kMmaWarps * 32, 0, s>>>(a);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
 // OR-group width: the widest G whose expected lower bound on a random pair,
 // (2W/G) * 32 * (1 - 2^-G), stays clear of the typical first bound.
 int choose_group(int W, int typical_thr) {
@@ -371,17 +581,10 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         const int G = choose_group(W, hthr[nq / 2]);
 #endif
 
-        const uint32_t qtiles = (nq + kLsQueries - 1) / kLsQueries;
-        // enough CTA columns to fill the GPU about 4 times over
-        uint64_t target = static_cast<uint64_t>(dev.sms) * 4;
-        uint64_t splits = (target + qtiles - 1) / qtiles;
-        const uint64_t max_splits = (n + kLsTile - 1) / kLsTile;
-        if (splits > max_splits) splits = max_splits;
-        if (splits < 1) splits = 1;
-        if (splits > 65535) splits = 65535;
-        uint64_t split_len = (n + splits - 1) / splits;
-        split_len = (split_len + kLsTile - 1) / kLsTile * kLsTile;
-        splits = (n + split_len - 1) / split_len;
+        // the popcount form unless the tensor-core form (fp8 products) is asked for
+        const bool tensor = scan_kernel_choice() == MIH_SCAN_TENSOR;
+        const ScanGrid sg = scan_grid(n, nq, tensor ? mma_queries_per_cta(W) : kLsQueries, dev.sms);
+        const uint64_t split_len = sg.split_len;
 
         ScanArgs a;
         memset(&a, 0, sizeof(a));
@@ -398,11 +601,12 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         a.buf = buf;
         a.cap = cap;
         a.cnt = cnt;
-        const dim3 grid(qtiles, static_cast<unsigned>(splits));
+        const dim3 grid = sg.grid;
         main_kernel_begin(s);
         {
             KernelSpan ks(s, MIH_PROF_SCAN);
-            MIH_TRY(launch_scan(a, W, G, grid, s));
+            if (tensor) MIH_TRY(launch_scan_mma(a, W, grid, s));
+            else MIH_TRY(launch_scan(a, W, G, grid, s));
         }
         main_kernel_end(s);
 
@@ -431,7 +635,8 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
             b.base = need;
             b.second_pass = 1;
             b.err = err;
-            MIH_TRY(launch_scan(b, W, 1, grid, s));
+            if (tensor) MIH_TRY(launch_scan_mma(b, W, grid, s));
+            else MIH_TRY(launch_scan(b, W, 1, grid, s));
             int herr = 0;
             MIH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
             MIH_CUDA(cudaStreamSynchronize(s));

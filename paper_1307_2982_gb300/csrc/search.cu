@@ -511,10 +511,17 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
     uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned long long total_chunks = a.chunk_off[a.nq];
     constexpr uint32_t kSlice = slice_entries<W, ALIGNED>();
-    for (;;) {
-        unsigned long long c = 0;
-        if (lane == 0) c = atomicAdd(a.chunk_next, 1ull);
-        c = __shfl_sync(0xFFFFFFFFu, c, 0);
+    // Chunk indices: the warp's own index first (no atomic), then nwarps plus
+    // the values of a shared counter.  Lane 0 grabs the next index before the
+    // current chunk runs and the warp reads it afterwards, so the atomic's round
+    // trip is off the critical path.  An index a warp grabbed but does not run
+    // lies at or beyond total_chunks (the counter only grows).
+    const unsigned long long nwarps = static_cast<unsigned long long>(gridDim.x) * (blockDim.x >> 5);
+    unsigned long long c = static_cast<unsigned long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    unsigned long long pending = 0;
+    if (lane == 0) pending = atomicAdd(a.chunk_next, 1ull);
+    for (;; c = nwarps + __shfl_sync(0xFFFFFFFFu, pending, 0), pending = lane == 0 ? atomicAdd(a.chunk_next, 1ull)
+                                                                                   : 0ull) {
         if (c >= total_chunks) break;
         // query owning chunk c: the last q with chunk_off[q] <= c, by a 32-ary
         // search (every lane probes one point per round; chunk_off[lo] <= c <
@@ -1388,7 +1395,7 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
                                 int32_t* __restrict__ hist_done, uint32_t* __restrict__ cnt1, uint32_t cap,
                                 unsigned long long* __restrict__ qstats, unsigned int* __restrict__ active,
                                 const TableDesc* __restrict__ tables, int m, uint8_t* __restrict__ exh,
-                                long long scan_budget, uint32_t* __restrict__ next_chunks) {
+                                long long scan_budget, uint32_t* __restrict__ next_chunks, int tail_from) {
     __shared__ int s_len[kMaxTables];
     for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
     __syncthreads();
@@ -1434,12 +1441,16 @@ __global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32
                 if (first_reach >= 0 && (bound[q] < 0 || first_reach < bound[q])) bound[q] = first_reach;
                 t_lo[q] = t + 1;
             }
-            t_hi[q] = t + 1;
-            // Once the next ring alone would push the lookups past the budget,
+            // one Alg. 3 step per wave, two from step tail_from on (every code
+            // within t bits is known after steps 0..t, so the next stopping
+            // test is exact either way)
+            const int steps = (tail_from >= 0 && t + 1 >= tail_from) ? 2 : 1;
+            t_hi[q] = t + steps;
+            // Once the next steps alone would push the lookups past the budget,
             // verifying every remaining code once is cheaper (Sec. 3 cost model:
             // a lookup costs about one candidate test).
             if (scan_budget >= 0 &&
-                qstats[4ull * q] + steps_lookups(s_len, m, t + 1, t + 1) > static_cast<unsigned long long>(scan_budget))
+                qstats[4ull * q] + steps_lookups(s_len, m, t + 1, t + steps) > static_cast<unsigned long long>(scan_budget))
                 exh[q] = 1;
             // chunks of the next wave's steps, for its planning
             next_chunks[q] = static_cast<uint32_t>(query_chunks(s_len, m, n, t_lo, t_hi, exh, q));
@@ -2036,12 +2047,26 @@ mih_status capture_stream(cudaStream_t* out) {
 
 struct GraphGuard {
     cudaGraph_t g = nullptr;
-    cudaGraphExec_t e = nullptr;
     ~GraphGuard() {
-        if (e) cudaGraphExecDestroy(e);
         if (g) cudaGraphDestroy(g);
     }
 };
+
+// One instantiated wave graph per device and host thread, reused across calls:
+// each call captures its body anew and updates the cached executable in place
+// (cudaGraphExecUpdate keeps the instantiation when the topology matches, and
+// a thread's previous launch has finished because every call synchronises its
+// stream before returning); when the update is refused the call instantiates
+// a new one.
+struct ExecCache {
+    static constexpr int kDevs = 64;
+    cudaGraphExec_t e[kDevs] = {};
+    ~ExecCache() {
+        for (cudaGraphExec_t x : e)
+            if (x) cudaGraphExecDestroy(x);
+    }
+};
+thread_local ExecCache t_exec;
 
 // Runs body(cs) -- launches recorded on the capture stream cs -- as the body of
 // a while-loop graph node on stream s, the first iteration unconditionally.
@@ -2074,9 +2099,27 @@ mih_status launch_while_graph(GraphGuard& gg, cudaStream_t s, uint64_t* body_lau
     }
     MIH_CUDA(ce);
     *body_launches = launches_so_far() - l0;
-    MIH_CUDA(cudaGraphInstantiate(&gg.e, gg.g, 0));
+    int d = 0;
+    MIH_CUDA(cudaGetDevice(&d));
+    if (d < 0 || d >= ExecCache::kDevs) {
+        set_error("device ordinal %d out of range", d);
+        return MIH_EINVAL;
+    }
+    cudaGraphExec_t& exec = t_exec.e[d];
+    bool updated = false;
+    if (exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(exec, gg.g, &info) == cudaSuccess) {
+            updated = true;
+        } else {
+            cudaGetLastError();
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+    }
+    if (!updated) MIH_CUDA(cudaGraphInstantiate(&exec, gg.g, 0));
     main_kernel_begin(s);  // the span covers every wave (with its planning and stopping test)
-    const cudaError_t le = cudaGraphLaunch(gg.e, s);
+    const cudaError_t le = cudaGraphLaunch(exec, s);
     main_kernel_end(s);
     MIH_CUDA(le);
     return MIH_OK;
@@ -2358,7 +2401,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         KernelSpan ks(ws_s, MIH_PROF_STOP, cs == nullptr);
         knn_stop_kernel<<<grid1(32ull * nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
                                                     hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
-                                                    exh, budget, wave_chunks);
+                                                    exh, budget, wave_chunks, query_stats ? -1 : ix->tail_from);
         MIH_LAUNCH_CHECK();
         return MIH_OK;
     };
@@ -2486,6 +2529,23 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
         stats->candidates_sliced = hs;
     }
     MIH_CUDA(cudaStreamSynchronize(s));
+    return MIH_OK;
+}
+
+// CSR offsets of per-query k: out[i] = k[0] + ... + k[i-1], out[nq] = total.
+mih_status mih_k_offsets(const uint32_t* k, uint32_t nq, uint64_t* out_offsets, void* stream) {
+    clear_error();
+    if (nq > (1u << 23)) {
+        set_error("mih_k_offsets: nq must be at most 2^23");
+        return MIH_EINVAL;
+    }
+    MIH_TRY(check_device_ptr(out_offsets, "out_offsets"));
+    if (nq > 0) MIH_TRY(check_device_ptr(k, "k"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace ws(s);
+    widen_counts_kernel<<<grid1(static_cast<uint64_t>(nq) + 1), 256, 0, s>>>(k, nq, out_offsets);
+    MIH_LAUNCH_CHECK();
+    MIH_TRY(scan_exclusive_u64(out_offsets, out_offsets, static_cast<size_t>(nq) + 1, ws));
     return MIH_OK;
 }
 

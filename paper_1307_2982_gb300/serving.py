@@ -123,8 +123,9 @@ class MihServer:
                         qh = torch.from_numpy(np.ascontiguousarray(req.codes[idx, :W]).view(np.int64)).pin_memory()
                         kh = torch.from_numpy(req.k[idx].astype(np.int32)).pin_memory()
                         qd = qh.to(dev, non_blocking=True)
-                        kd = kh.to(dev, non_blocking=True)
-                        r = mih_knn(ix, qd, kd, stream=stream)
+                        # host k: the binding takes the CSR offsets from the host
+                        # values, with no device synchronisation
+                        r = mih_knn(ix, qd, kh, stream=stream)
                         ids = r["ids"].to("cpu", non_blocking=True)
                         dist = r["dist"].to("cpu", non_blocking=True)
                         off = r["offsets"].to("cpu", non_blocking=True)

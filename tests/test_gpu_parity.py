@@ -105,6 +105,35 @@ def test_linscan_and_mih_knn_match_oracle(gpu_lib, orc, kind, q, n, nq, ms):
         ix.free()
 
 
+@pytest.mark.parametrize("kind,q,n,nq", [("uniform", 64, 100_003, 300), ("lsh", 128, 200_003, 257),
+                                         ("lsh", 256, 60_001, 130), ("ties", 128, 30_000, 100),
+                                         ("uniform", 128, 37, 9)])
+@pytest.mark.parametrize("scan", [1, 2])
+def test_linscan_kernels_match_oracle(gpu_lib, orc, kind, q, n, nq, scan):
+    """Both forms of the linear scan (Sec. 5.2) give the definition's answer:
+    xor + popcount (1) and fp8 tensor-core products of +-1 codes (2).  Ragged
+    code and query counts, tie-heavy codes (the bounded buffers overflow and
+    the second pass collects), k above n, per-query k."""
+    import torch
+
+    mih = gpu_lib
+    db, qs = workload(kind, q, n, nq, seed=17)
+    codes, queries = to_dev(db), to_dev(qs)
+    try:
+        mih.mih_set_scan_kernel(scan)
+        for k in (1, 10, 100, 1000):
+            want_ids, want_dist = orc.knn(db, qs, k)
+            r = mih.linscan_knn(codes, q, queries, k)
+            assert np.array_equal(ids_of(r["ids"]), want_ids), (scan, k)
+            assert np.array_equal(host(r["dist"]), want_dist), (scan, k)
+        ks = synth.per_query_k(nq, seed=5, kmax=300)
+        off, wi, wd = orc.knn(db, qs, ks)
+        r = mih.linscan_knn(codes, q, queries, torch.from_numpy(ks.astype(np.int32)).cuda())
+        assert np.array_equal(ids_of(r["ids"]), wi) and np.array_equal(host(r["dist"]), wd)
+    finally:
+        mih.mih_set_scan_kernel(0)
+
+
 @pytest.mark.parametrize("table_kind,inline", [(1, 1), (2, 1), (1, -1), (2, -1)])
 def test_table_kinds_agree(gpu_lib, orc, table_kind, inline):
     """Direct and sparse tables (Sec. 6), with or without inline codes, agree."""
@@ -209,6 +238,48 @@ def test_graph_and_host_executors_agree(gpu_lib, orc, kind, q, m, n):
                 assert np.array_equal(host(rg["query_stats"]), host(rh["query_stats"]))
 
 
+@pytest.mark.parametrize("kind,q,m,n", [("lsh", 128, 4, 200_003), ("uniform", 64, 3, 80_000),
+                                        ("lsh", 256, 9, 60_001), ("ties", 128, 4, 30_000)])
+def test_two_step_waves_keep_results(gpu_lib, orc, kind, q, m, n):
+    """Two Alg. 3 steps per wave (from step 1, or the default step 2m) give the
+    oracle's answer, as one step per wave does, in no more waves."""
+    import torch
+
+    mih = gpu_lib
+    db, qs = workload(kind, q, n, 257, seed=23)
+    codes, queries = to_dev(db), to_dev(qs)
+    ks = synth.per_query_k(257, seed=6, kmax=1000)
+    off, wi, wd = orc.knn(db, qs, ks)
+    waves = {}
+    for tail in (-1, 1, 0):
+        ix = mih.mih_build(codes, q, m, tail_from=tail)
+        r = mih.mih_knn(ix, queries, torch.from_numpy(ks.astype(np.int32)).cuda())
+        assert np.array_equal(ids_of(r["ids"]), wi), tail
+        assert np.array_equal(host(r["dist"]), wd), tail
+        waves[tail] = r["stats"]["waves"]
+        ix.free()
+    assert waves[1] <= waves[-1] and waves[0] <= waves[-1], waves
+
+
+def test_reused_wave_graph_across_calls(gpu_lib, orc):
+    """Consecutive graph-executor calls reuse one instantiated graph per thread
+    (updated in place, or instantiated again when the shape changes): calls
+    that alternate code length, m and batch size each give the oracle's answer."""
+    mih = gpu_lib
+    db128, qs128 = workload("lsh", 128, 60_000, 300, seed=41)
+    db64, qs64 = workload("uniform", 64, 40_000, 300, seed=42)
+    ix128 = mih.mih_build(to_dev(db128), 128, 4, executor=mih.MIH_EXEC_GRAPH)
+    ix64 = mih.mih_build(to_dev(db64), 64, 3, executor=mih.MIH_EXEC_GRAPH)
+    for ix, db, qs, nq, k in ((ix128, db128, qs128, 300, 10), (ix128, db128, qs128, 300, 10),
+                              (ix64, db64, qs64, 3, 7), (ix128, db128, qs128, 1, 100),
+                              (ix64, db64, qs64, 300, 50), (ix128, db128, qs128, 257, 10)):
+        want_ids, want_dist = orc.knn(db, qs[:nq], k)
+        r = mih.mih_knn(ix, to_dev(qs[:nq]), k)
+        assert np.array_equal(ids_of(r["ids"]), want_ids) and np.array_equal(host(r["dist"]), want_dist)
+    ix128.free()
+    ix64.free()
+
+
 def test_per_query_k_and_padding(gpu_lib, orc):
     mih = gpu_lib
     import torch
@@ -220,7 +291,9 @@ def test_per_query_k_and_padding(gpu_lib, orc):
     off, want_ids, want_dist = orc.knn(db, qs, ks)
     kt = torch.from_numpy(ks.astype(np.int32)).cuda()
     ix = mih.mih_build(codes, q, 3)
-    for r in (mih.mih_knn(ix, queries, kt), mih.linscan_knn(codes, q, queries, kt)):
+    # device k (offsets by mih_k_offsets) and host k (offsets from the host values)
+    for r in (mih.mih_knn(ix, queries, kt), mih.linscan_knn(codes, q, queries, kt),
+              mih.mih_knn(ix, queries, ks), mih.mih_knn(ix, queries, torch.from_numpy(ks.astype(np.int32)))):
         assert np.array_equal(host(r["offsets"]), off.astype(np.int64))
         assert np.array_equal(ids_of(r["ids"]), want_ids)
         assert np.array_equal(host(r["dist"]), want_dist)
