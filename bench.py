@@ -347,6 +347,17 @@ def run_ours(a):
     torch.cuda.synchronize()
     build_ms = ev0.elapsed_time(ev1)
     info = index.info()
+    # launch choices of the k-NN waves (slice-kernel shape, two-step start),
+    # timed on the hold-out queries and kept in the index
+    search_tuning = None
+    if not a.no_autotune and a.tail_from == 0:
+        hold = make_codes(kind, 1000, q, 5, dev)
+        t0 = time.perf_counter()
+        best, table = mih.mih_tune_search(index, hold, k if k != "kper" else 100)
+        search_tuning = {"chosen": best, "ms_per_query": table, "holdout_queries": 1000,
+                         "seconds": time.perf_counter() - t0}
+        del hold
+        torch.cuda.empty_cache()
 
     # outputs preallocated (the call writes into caller buffers)
     if kt is None:
@@ -598,7 +609,9 @@ def run_ours(a):
                    "substring_bits": info["substring_length"], "table_kind": info["table_kind"],
                    "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s,
                    "inline_codes": info["inline_codes"], "executor": a.executor, "substrings": substrings,
-                   "tail_from": a.tail_from if a.tail_from else 2 * m,
+                   "tail_from": (search_tuning["chosen"]["tail_from"] if search_tuning else
+                                 (a.tail_from if a.tail_from else 2 * m)),
+                   "search_tuning": search_tuning,
                    "autotune": tune},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "mih_stats_per_step": {kk: v / a.steps for kk, v in stats_acc.items()},

@@ -119,8 +119,18 @@ typedef struct {
                               and 2 hold for any partition into m disjoint
                               substrings); only the work per step changes.
                               mih_cost_layout proposes lengths. */
-    int32_t reserved[6];   /* must be zero */
+    int32_t slice_shape;   /* Shape of the kernel that streams big buckets in the
+                              k-NN waves (a launch choice; results unchanged):
+                              MIH_SLICE_SHAPE_4K_8W (default) 4 KB stages, 8 warps
+                              per CTA, 2 stages in flight per warp;
+                              MIH_SLICE_SHAPE_8K_4W 8 KB stages, 4 warps;
+                              MIH_SLICE_SHAPE_4K_8W_3S 4 KB stages, 8 warps, 3 in
+                              flight.  mih_tune_search picks one by timing. */
+    int32_t reserved[5];   /* must be zero */
 } mih_params;
+
+/* mih_params.slice_shape values. */
+enum { MIH_SLICE_SHAPE_4K_8W = 0, MIH_SLICE_SHAPE_8K_4W = 1, MIH_SLICE_SHAPE_4K_8W_3S = 2 };
 
 /* mih_params.executor (not part of the paper: a launch strategy). */
 enum {
@@ -323,6 +333,29 @@ MIH_API mih_status mih_autotune(const uint64_t *codes, uint64_t n, int q, const 
                                 uint32_t nq, uint32_t k, const int *candidates, int n_candidates,
                                 const mih_params *params, void *stream, int *best_m,
                                 double *ms_per_query);
+
+/* ------------------------------------------------------------------------
+ * mih_tune_search -- the launch choices of an index's k-NN waves, picked by
+ * timing on hold-out queries (the selection by validation of Sec. 6, applied
+ * to the launch shapes; results do not depend on them): every combination of
+ * the slice kernel's shape (mih_params.slice_shape) and the step from which
+ * queries run two steps per wave (mih_params.tail_from: 2m, m, never) runs
+ * one untimed and one timed mih_knn of the hold-out queries with k; the
+ * fastest is kept in the index.  Do not search the index from other threads
+ * during the call.
+ * queries, nq   device, hold-out queries (1 <= nq <= 2^23); k in 1..MIH_MAX_K.
+ * best          host out, nullable: {slice_shape, tail_from} chosen.
+ * ms_per_query  host out, nullable, double[3 * 3]: entry [shape * 3 + tail],
+ *               tail 0 = from step 2m, 1 = from step m, 2 = never.
+ * Synchronises `stream`.  Errors: as mih_knn.
+ */
+typedef struct {
+    int32_t slice_shape;
+    int32_t tail_from;
+} mih_search_tuning;
+
+MIH_API mih_status mih_tune_search(mih_index *index, const uint64_t *queries, uint32_t nq, uint32_t k,
+                                   void *stream, mih_search_tuning *best, double *ms_per_query);
 
 /* ------------------------------------------------------------------------
  * linscan_knn_noalloc -- linscan_knn for callers that cannot allocate device

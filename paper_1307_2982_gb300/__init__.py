@@ -26,6 +26,8 @@ MIH_OK, MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EOVERFLOW, MIH_ETIMEOUT, MIH_EINT
 MIH_TABLE_AUTO, MIH_TABLE_DIRECT, MIH_TABLE_SPARSE = 0, 1, 2
 MIH_EXEC_AUTO, MIH_EXEC_HOST, MIH_EXEC_GRAPH = 0, 1, 2
 MIH_SCAN_AUTO, MIH_SCAN_POPC, MIH_SCAN_TENSOR = 0, 1, 2
+MIH_SLICE_SHAPE_4K_8W, MIH_SLICE_SHAPE_8K_4W, MIH_SLICE_SHAPE_4K_8W_3S = 0, 1, 2
+SLICE_SHAPES = ("4KB stages x 8 warps x 2", "8KB stages x 4 warps x 2", "4KB stages x 8 warps x 3")
 MIH_MAX_K = 8192
 PAD_ID = 0xFFFFFFFF
 
@@ -35,7 +37,7 @@ EXPORTS = (
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
     "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation", "mih_set_wait_limit",
     "mih_cost_layout", "mih_autotune_layout", "mih_merge_topk", "mih_measure_ceilings",
-    "mih_set_scan_kernel", "mih_k_offsets",
+    "mih_set_scan_kernel", "mih_k_offsets", "mih_tune_search",
 )
 
 
@@ -49,7 +51,8 @@ class mih_params(ctypes.Structure):
     _fields_ = [("table_kind", ctypes.c_int32), ("scan_factor", ctypes.c_int32),
                 ("inline_codes", ctypes.c_int32), ("probe", ctypes.c_int32), ("executor", ctypes.c_int32),
                 ("tail_from", ctypes.c_int32), ("bit_order", ctypes.POINTER(ctypes.c_int32)),
-                ("substring_length", ctypes.POINTER(ctypes.c_int32)), ("reserved", ctypes.c_int32 * 6)]
+                ("substring_length", ctypes.POINTER(ctypes.c_int32)), ("slice_shape", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class mih_stats(ctypes.Structure):
@@ -132,6 +135,8 @@ def load():
     lib.mih_cost_layout.restype = ctypes.c_double
     lib.mih_autotune_layout.argtypes = [P, u64, i32, P, u32, u32, i32, P, P, P, P]
     lib.mih_autotune_layout.restype = st
+    lib.mih_tune_search.argtypes = [P, P, u32, u32, P, P, P]
+    lib.mih_tune_search.restype = st
     lib.mih_k_offsets.argtypes = [P, u32, P, P]
     lib.mih_k_offsets.restype = st
     lib.mih_set_scan_kernel.argtypes = [i32]
@@ -330,7 +335,7 @@ class MihIndex:
 
 def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_factor: int = 0,
               inline_codes: int = 0, probe: int = 0, executor: int = MIH_EXEC_AUTO, bit_order=None,
-              substring_length=None, tail_from: int = 0, stream=None) -> MihIndex:
+              substring_length=None, tail_from: int = 0, slice_shape: int = 0, stream=None) -> MihIndex:
     ptr, n = _codes_arg(codes, q)
     p = mih_params()
     p.table_kind = table_kind
@@ -339,6 +344,7 @@ def mih_build(codes, q: int, m: int, table_kind: int = MIH_TABLE_AUTO, scan_fact
     p.probe = probe
     p.executor = executor
     p.tail_from = tail_from
+    p.slice_shape = slice_shape
     if bit_order is not None:
         order = np.ascontiguousarray(bit_order, dtype=np.int32)
         if order.shape != (q,):
@@ -382,6 +388,24 @@ def mih_autotune_layout(codes, q: int, queries, k: int, m: int, stream=None, **b
     _check(load().mih_autotune_layout(cptr, n, q, qptr, nq, k, m, ctypes.byref(p), _stream(stream),
                                       out.ctypes.data, times), "mih_autotune_layout")
     return [int(x) for x in out], {"uniform": times[0], "cost_model": times[1]}
+
+
+class mih_search_tuning(ctypes.Structure):
+    _fields_ = [("slice_shape", ctypes.c_int32), ("tail_from", ctypes.c_int32)]
+
+
+def mih_tune_search(index: MihIndex, queries, k: int, stream=None):
+    """Slice-kernel shape and two-step start of the index's k-NN waves, timed on
+    hold-out queries and kept in the index.  Returns (best dict, {(shape, tail): ms per query})."""
+    qptr, nq = _codes_arg(queries, index.q)
+    best = mih_search_tuning()
+    times = (ctypes.c_double * 9)()
+    _check(load().mih_tune_search(index.handle, qptr, nq, k, _stream(stream), ctypes.byref(best), times),
+           "mih_tune_search")
+    tails = ("2m", "m", "never")
+    table = {f"{SLICE_SHAPES[sh]} / tail {tails[t]}": times[sh * 3 + t] for sh in range(3) for t in range(3)
+             if times[sh * 3 + t] >= 0}
+    return {"slice_shape": SLICE_SHAPES[best.slice_shape], "tail_from": int(best.tail_from)}, table
 
 
 def mih_free(index: MihIndex):

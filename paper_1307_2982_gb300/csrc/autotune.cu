@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "index.h"
 #include "launch.h"
 
 extern "C" mih_status mih_autotune(const uint64_t* codes, uint64_t n, int q, const uint64_t* queries, uint32_t nq,
@@ -196,4 +197,77 @@ extern "C" mih_status mih_autotune_layout(const uint64_t* codes, uint64_t n, int
     const int32_t* best = (!same && t_cost < t_uni) ? cost_len.data() : uni_len.data();
     for (int j = 0; j < m; ++j) best_length[j] = best[j];
     return MIH_OK;
+}
+
+// Launch choices of an index's k-NN waves by timing on hold-out queries: the
+// slice kernel's shape x the step from which queries run two steps per wave.
+extern "C" mih_status mih_tune_search(mih_index* ix, const uint64_t* queries, uint32_t nq, uint32_t k, void* stream,
+                                      mih_search_tuning* best, double* ms_per_query) {
+    using namespace mih;
+    clear_error();
+    if (!ix) {
+        set_error("mih_tune_search: index is NULL");
+        return MIH_EINVAL;
+    }
+    if (nq == 0 || k == 0 || k > MIH_MAX_K) {
+        set_error("mih_tune_search: need at least one hold-out query and 1 <= k <= %u", MIH_MAX_K);
+        return MIH_EINVAL;
+    }
+    constexpr int kShapes = 3, kTails = 3;
+    if (ms_per_query)
+        for (int i = 0; i < kShapes * kTails; ++i) ms_per_query[i] = -1.0;
+    const int tails[kTails] = {2 * ix->m, ix->m, -1};
+    const int old_shape = ix->slice_shape, old_tail = ix->tail_from;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* ids = nullptr;
+    int32_t* dist = nullptr;
+    MIH_CUDA(cudaMalloc(&ids, sizeof(uint32_t) * nq * static_cast<size_t>(k)));
+    if (cudaMalloc(&dist, sizeof(int32_t) * nq * static_cast<size_t>(k)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ids);
+        set_error("mih_tune_search: output allocation failed");
+        return MIH_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    mih_status st = MIH_OK;
+    double best_ms = -1.0;
+    int best_shape = old_shape, best_tail = old_tail;
+    // without inline codes big buckets go through the by-id kernel: the shape
+    // does not apply
+    const int shapes = ix->inline_codes ? kShapes : 1;
+    for (int sh = 0; sh < shapes && st == MIH_OK; ++sh) {
+        for (int ti = 0; ti < kTails && st == MIH_OK; ++ti) {
+            ix->slice_shape = sh;
+            ix->tail_from = tails[ti];
+            st = mih_knn(ix, queries, nq, nullptr, k, nullptr, ids, dist, nullptr, nullptr, stream);   // warm
+            if (st != MIH_OK) break;
+            cudaEventRecord(e0, s);
+            st = mih_knn(ix, queries, nq, nullptr, k, nullptr, ids, dist, nullptr, nullptr, stream);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            if (st != MIH_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per_q = ms / nq;
+            if (ms_per_query) ms_per_query[sh * kTails + ti] = per_q;
+            if (best_ms < 0 || per_q < best_ms) {
+                best_ms = per_q;
+                best_shape = sh;
+                best_tail = tails[ti];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(ids);
+    cudaFree(dist);
+    ix->slice_shape = st == MIH_OK ? best_shape : old_shape;
+    ix->tail_from = st == MIH_OK ? best_tail : old_tail;
+    if (best) {
+        best->slice_shape = ix->slice_shape;
+        best->tail_from = ix->tail_from;
+    }
+    return st;
 }

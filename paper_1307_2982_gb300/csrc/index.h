@@ -24,5 +24,6 @@ struct mih_index {
     int probe = 1024;                           // bound-probe entries per bucket (0 = off)
     int executor = 0;                           // MIH_EXEC_* for the k-NN wave loop
     int tail_from = 0;                          // step from which queries run two steps per wave (-1: never)
+    int slice_shape = 0;                        // slice-kernel shape of the k-NN waves (MIH_SLICE_SHAPE_*)
     int32_t* bit_order = nullptr;               // device, q entries: optimised substrings (Sec. 5.5), or null
 };

@@ -53,6 +53,7 @@ struct ScanArgs {
     const uint64_t* base;      // second pass only: [nq + 1]
     int second_pass;
     int* err;                  // set when a second-pass write would leave its query's range
+    int* timeout;              // tensor-core form: set when a bounded wait on a stage copy gave up
 };
 
 __device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform, uint32_t q, uint64_t n) {
@@ -188,11 +189,13 @@ __global__ void __launch_bounds__(kLsThreads) linscan_kernel(ScanArgs a) {
 // 32-bit code word is one K-step of mma.m16n8k32.
 //
 // A warp holds the A fragments of its 16 MT queries in registers for the whole
-// scan and streams 8 NT codes per step, building their B fragments from the
-// code words; the CTA's warps scan the same codes (L1 reuse) for different
-// queries.  A pair is kept when dot >= q - 2 thr_q, i.e. d <= thr_q; the warp
+// scan and takes 8 NT codes per step, building their B fragments from code
+// words that the CTA stages in shared memory; the CTA's warps scan the same
+// codes for different queries.  A pair is kept when dot >= q - 2 thr_q, i.e. d <= thr_q; the warp
 // only looks at single pairs when one of its lanes has such a pair.
 constexpr int kMmaWarps = 4;
+constexpr int kMmaStageCodes = 256;   // codes per shared-memory stage
+constexpr int kMmaSlots = 3;          // stages in flight per CTA (a ring of slots)
 
 template <int W>
 struct MmaShape {
@@ -213,18 +216,52 @@ __device__ __forceinline__ void mma_e4m3(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// A W-word code from shared memory (16-byte loads for W >= 2).
+template <int W>
+__device__ __forceinline__ Code<W> smem_code(const uint64_t* sc, uint32_t i) {
+    Code<W> c;
+    if constexpr (W == 1) {
+        c.w[0] = sc[i];
+    } else {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(sc + static_cast<uint64_t>(i) * W);
+#pragma unroll
+        for (int h = 0; h < W / 2; ++h) {
+            const ulonglong2 v = p[h];
+            c.w[2 * h] = v.x;
+            c.w[2 * h + 1] = v.y;
+        }
+    }
+    return c;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The CTA's codes arrive in stages of kMmaStageCodes, copied into a ring of
+// kMmaSlots shared-memory slots by the bulk-copy engine (thread 0 issues,
+// completion counted on a per-slot mbarrier), so the warps read code words
+// from shared memory.  Every wait is bounded and the decision to go on is
+// taken by the whole CTA; on expiry the CTA raises a.timeout, waits (bounded)
+// for its copies in flight and leaves.
 template <int W>
 __global__ void __launch_bounds__(kMmaWarps * 32) linscan_mma_kernel(ScanArgs a) {
     constexpr int KS = 2 * W;                       // K-steps: 32-bit words per code
     constexpr int MT = MmaShape<W>::MT, NT = MmaShape<W>::NT;
     constexpr int QW = 16 * MT, QC = QW * kMmaWarps, CT = 8 * NT;
-    constexpr int kRefreshSteps = kLsRefresh * kLsTile / CT;
+    constexpr int kRefreshStages = kLsRefresh * kLsTile / kMmaStageCodes;
+    __shared__ __align__(16) uint64_t s_codes[kMmaSlots][kMmaStageCodes * W];
+    __shared__ __align__(8) uint64_t s_bar[kMmaSlots];
     __shared__ int s_thr[QC];
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id(), g = lane >> 2, t = lane & 3;
     const uint32_t q0 = blockIdx.x * QC;
     const uint32_t nql = min(static_cast<uint32_t>(QC), a.nq - q0);
     for (int i = threadIdx.x; i < QC; i += blockDim.x) s_thr[i] = static_cast<uint32_t>(i) < nql ? a.thr[q0 + i] : -1;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kMmaSlots; ++i) mbar_init(&s_bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     // A fragments: rows g and g + 8 of each query tile; bits 4t..4t+3 of a
     // word in registers 0/1, bits 16+4t..16+4t+3 in registers 2/3
@@ -259,85 +296,115 @@ __global__ void __launch_bounds__(kMmaWarps * 32) linscan_mma_kernel(ScanArgs a)
     load_cuts();
     const uint64_t begin = static_cast<uint64_t>(blockIdx.y) * a.split_len;
     const uint64_t end = min(a.n, begin + a.split_len);
-    // code words of the current step; the next step's are loaded before this
-    // step's products run
-    uint32_t cw[NT][KS];
-    auto load_step = [&](uint64_t base, uint32_t (&dst)[NT][KS]) {
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const uint64_t i = base + nt * 8 + g;
-            Code<W> v{};
-            if (i < end) v = load_code<W>(a.codes, i);
-#pragma unroll
-            for (int ks = 0; ks < KS; ++ks) dst[nt][ks] = static_cast<uint32_t>(v.w[ks >> 1] >> (32 * (ks & 1)));
+    const uint64_t nstages = (end - begin + kMmaStageCodes - 1) / kMmaStageCodes;
+    // thread 0: copy stage st into its slot.  Whole 16-byte multiples go by
+    // bulk copy; with 8-byte codes an odd last code is stored by a plain load,
+    // before the arrival that publishes the stage.
+    auto issue = [&](uint64_t st) {
+        const uint64_t c0 = begin + st * kMmaStageCodes;
+        const uint32_t cnt = static_cast<uint32_t>(min(static_cast<uint64_t>(kMmaStageCodes), end - c0));
+        const int slot = static_cast<int>(st % kMmaSlots);
+        uint64_t* dst = s_codes[slot];
+        uint32_t bulk = cnt;
+        if constexpr (W == 1) {
+            bulk = cnt & ~1u;
+            if (bulk < cnt) dst[cnt - 1] = __ldg(a.codes + c0 + cnt - 1);
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier reads of the slot are done
+        if (bulk > 0) bulk_copy_to_smem(dst, a.codes + c0 * W, bulk * 8u * W, &s_bar[slot]);
+        else mbar_arrive(&s_bar[slot]);
     };
-    load_step(begin, cw);
-    int step_no = 0;
-    for (uint64_t base = begin; base < end; base += CT, ++step_no) {
-        uint32_t nx[NT][KS];
-        load_step(base + CT, nx);
-        float D[MT][NT][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) D[mt][nt][e] = 0.5f - cut[mt][e >> 1];
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            uint32_t b0[NT], b1[NT];
+    if (threadIdx.x == 0)
+        for (uint64_t st = 0; st < kMmaSlots && st < nstages; ++st) issue(st);
+    uint32_t parities = 0u;
+    for (uint64_t st = 0; st < nstages; ++st) {
+        const int slot = static_cast<int>(st % kMmaSlots);
+        const bool ok = mbar_wait_bounded(&s_bar[slot], (parities >> slot) & 1u, kWaitNs);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                if (a.timeout) atomicExch(a.timeout, 1);
+                // the copies still in flight land before the CTA leaves
+                for (uint64_t s2 = st; s2 < st + kMmaSlots && s2 < nstages; ++s2) {
+                    const int sl = static_cast<int>(s2 % kMmaSlots);
+                    mbar_wait_bounded(&s_bar[sl], (parities >> sl) & 1u, kWaitNs);
+                }
+            }
+            __syncthreads();
+            return;
+        }
+        parities ^= 1u << slot;
+        const uint64_t c0 = begin + st * kMmaStageCodes;
+        const uint32_t cnt = static_cast<uint32_t>(min(static_cast<uint64_t>(kMmaStageCodes), end - c0));
+        const uint64_t* sc = s_codes[slot];
+        for (uint32_t lb = 0; lb < cnt; lb += CT) {
+            uint32_t cw[NT][KS];
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-                b0[nt] = pm1_e4m3x4((cw[nt][ks] >> (4 * t)) & 0xFu);
-                b1[nt] = pm1_e4m3x4((cw[nt][ks] >> (16 + 4 * t)) & 0xFu);
+                const uint32_t idx = lb + nt * 8 + g;
+                Code<W> v{};
+                if (idx < cnt) v = smem_code<W>(sc, idx);
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) cw[nt][ks] = static_cast<uint32_t>(v.w[ks >> 1] >> (32 * (ks & 1)));
             }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) mma_e4m3(D[mt][nt], A[mt][ks], b0[nt], b1[nt]);
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int ks = 0; ks < KS; ++ks) cw[nt][ks] = nx[nt][ks];
-        // accumulator e: row g + 8 (e >> 1) of the query tile, code 2t + (e & 1)
-        // of the code tile; a clear sign bit in the AND of all of them means
-        // some pair of this lane is kept
-        uint32_t signs = 0xFFFFFFFFu;
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) signs &= __float_as_uint(D[mt][nt][e]);
-        if (__any_sync(0xFFFFFFFFu, (signs >> 31) == 0u)) {
+            float D[MT][NT][4];
 #pragma unroll
             for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int h = e >> 1;
-                        const uint64_t i = base + nt * 8 + 2 * t + (e & 1);
-                        if (i >= end || (__float_as_uint(D[mt][nt][e]) >> 31) != 0u) continue;
-                        const int dot = __float2int_rn(D[mt][nt][e] - 0.5f + cut[mt][h]);
-                        const int d = (a.qbits - dot) >> 1;
-                        const uint32_t q = q0 + warp * QW + mt * 16 + g + 8 * h;
-                        const uint32_t id = static_cast<uint32_t>(i);
-                        const uint32_t p = atomicAdd(&a.cnt[q], 1u);
-                        if (!a.second_pass) {
-                            if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, id);
-                            atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.qbits + 1) + d], 1u);
-                        } else {
-                            const uint64_t slot = a.base[q] + p;
-                            if (slot < a.base[q + 1]) a.buf[slot] = pack_entry(d, id);
-                            else atomicExch(a.err, 1);
+                    for (int e = 0; e < 4; ++e) D[mt][nt][e] = 0.5f - cut[mt][e >> 1];
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                uint32_t b0[NT], b1[NT];
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    b0[nt] = pm1_e4m3x4((cw[nt][ks] >> (4 * t)) & 0xFu);
+                    b1[nt] = pm1_e4m3x4((cw[nt][ks] >> (16 + 4 * t)) & 0xFu);
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt) mma_e4m3(D[mt][nt], A[mt][ks], b0[nt], b1[nt]);
+            }
+            // accumulator e: row g + 8 (e >> 1) of the query tile, code 2t + (e & 1)
+            // of the code tile; a clear sign bit in the AND of all of them means
+            // some pair of this lane is kept
+            uint32_t signs = 0xFFFFFFFFu;
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) signs &= __float_as_uint(D[mt][nt][e]);
+            if (__any_sync(0xFFFFFFFFu, (signs >> 31) == 0u)) {
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int h = e >> 1;
+                            const uint32_t idx = lb + nt * 8 + 2 * t + (e & 1);
+                            if (idx >= cnt || (__float_as_uint(D[mt][nt][e]) >> 31) != 0u) continue;
+                            const int dot = __float2int_rn(D[mt][nt][e] - 0.5f + cut[mt][h]);
+                            const int d = (a.qbits - dot) >> 1;
+                            const uint32_t q = q0 + warp * QW + mt * 16 + g + 8 * h;
+                            const uint32_t id = static_cast<uint32_t>(c0 + idx);
+                            const uint32_t p = atomicAdd(&a.cnt[q], 1u);
+                            if (!a.second_pass) {
+                                if (p < a.cap) a.buf[static_cast<uint64_t>(q) * a.cap + p] = pack_entry(d, id);
+                                atomicAdd(&a.hist[static_cast<uint64_t>(q) * (a.qbits + 1) + d], 1u);
+                            } else {
+                                const uint64_t slot2 = a.base[q] + p;
+                                if (slot2 < a.base[q + 1]) a.buf[slot2] = pack_entry(d, id);
+                                else atomicExch(a.err, 1);
+                            }
                         }
-                    }
+            }
         }
-        if (!a.second_pass && (step_no % kRefreshSteps) == kRefreshSteps - 1) {
-            __syncthreads();
+        __syncthreads();   // every warp is done with this slot
+        if (threadIdx.x == 0 && st + kMmaSlots < nstages) issue(st + kMmaSlots);
+        if (!a.second_pass && (st % kRefreshStages) == kRefreshStages - 1) {
             for (uint32_t r = threadIdx.x; r < nql; r += blockDim.x) {
                 const uint32_t q = q0 + r;
                 const uint32_t kk = kk_of(a.kq, a.k_uniform, q, a.n);
@@ -582,7 +649,10 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
 #endif
 
         // the popcount form unless the tensor-core form (fp8 products) is asked for
-        const bool tensor = scan_kernel_choice() == MIH_SCAN_TENSOR;
+        // (its stage copies start on 16-byte boundaries: 8-byte codes must be
+        // 16-byte aligned for it)
+        const bool tensor = scan_kernel_choice() == MIH_SCAN_TENSOR &&
+                            (W >= 2 || reinterpret_cast<uintptr_t>(codes) % 16 == 0);
         const ScanGrid sg = scan_grid(n, nq, tensor ? mma_queries_per_cta(W) : kLsQueries, dev.sms);
         const uint64_t split_len = sg.split_len;
 
@@ -601,6 +671,12 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
         a.buf = buf;
         a.cap = cap;
         a.cnt = cnt;
+        int* timeout = nullptr;
+        if (tensor) {
+            MIH_TRY(ws.alloc(&timeout, 1));
+            MIH_CUDA(cudaMemsetAsync(timeout, 0, sizeof(int), s));
+            a.timeout = timeout;
+        }
         const dim3 grid = sg.grid;
         main_kernel_begin(s);
         {
@@ -614,7 +690,13 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
                                                               n_over);
         MIH_LAUNCH_CHECK();
         MIH_CUDA(cudaMemcpyAsync(&hover, n_over, sizeof(hover), cudaMemcpyDeviceToHost, s));
+        int htimeout = 0;
+        if (timeout) MIH_CUDA(cudaMemcpyAsync(&htimeout, timeout, sizeof(int), cudaMemcpyDeviceToHost, s));
         MIH_CUDA(cudaStreamSynchronize(s));
+        if (htimeout) {
+            set_error("linscan_knn: a bounded wait on a bulk copy expired");
+            return MIH_ETIMEOUT;
+        }
         if (hover > 0) {
             // Second pass over the database for queries whose buffer overflowed:
             // collect exactly the codes within d_k bits.
@@ -639,7 +721,12 @@ extern "C" mih_status linscan_knn(const uint64_t* codes, uint64_t n, int q, cons
             else MIH_TRY(launch_scan(b, W, 1, grid, s));
             int herr = 0;
             MIH_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            if (timeout) MIH_CUDA(cudaMemcpyAsync(&htimeout, timeout, sizeof(int), cudaMemcpyDeviceToHost, s));
             MIH_CUDA(cudaStreamSynchronize(s));
+            if (htimeout) {
+                set_error("linscan_knn: a bounded wait on a bulk copy expired");
+                return MIH_ETIMEOUT;
+            }
             if (herr) {
                 set_error("linscan_knn: second pass found more codes within d_k than counted");
                 return MIH_EINTERNAL;

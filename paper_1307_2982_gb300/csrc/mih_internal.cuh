@@ -179,6 +179,61 @@ __device__ __forceinline__ void lookup_bucket(const TableDesc& t, uint32_t key, 
     }
 }
 
+// ------------------------------------------------------- bulk async copies
+// Global -> shared copies by the bulk-copy engine (cp.async.bulk), completion
+// counted in bytes on an mbarrier, and bounded waits on that barrier.
+constexpr uint32_t kWaitHintNs = 20000;          // longest suspension of one try_wait
+constexpr uint64_t kWaitNs = 1000000000ull;      // a bulk copy not done after 1 s is an error
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `bar` with the given parity.  Each try_wait may
+// suspend the warp (up to kWaitHintNs, woken early when the phase completes)
+// instead of spinning, so waiting warps leave the issue slots to the warps
+// that verify codes.  Gives up after limit_ns of global time, and in any case
+// after a bounded number of polls (each takes at least a few nanoseconds).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    const uint32_t hint = limit_ns < kWaitHintNs ? static_cast<uint32_t>(limit_ns) : kWaitHintNs;
+    const uint64_t max_polls = limit_ns / 4u + 4096u;
+    uint64_t t0 = 0;
+    for (uint64_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint)
+            : "memory");
+        if (ok) return true;
+        if ((it & 7u) == 0) {
+            const uint64_t now = global_ns();
+            if (it == 0) t0 = now;
+            else if (now - t0 > limit_ns) return false;
+        }
+        if (it >= max_polls) return false;
+    }
+}
+
 // ---------------------------------------------------------------- warp utils
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 

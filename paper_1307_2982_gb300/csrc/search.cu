@@ -43,24 +43,24 @@ constexpr uint32_t kSliceEntries = 1024;   // big-bucket slice of whole codes
 #ifndef MIH_STAGE_BYTES
 #define MIH_STAGE_BYTES 4096
 #endif
-constexpr uint32_t kStageBytes = MIH_STAGE_BYTES;   // one shared-memory stage of the slice kernel
+constexpr uint32_t kDefaultStageBytes = MIH_STAGE_BYTES;   // one shared-memory stage of the slice kernel
 
 // Entries per stage of the slice kernel: whole codes (W uint64 words), or
 // records of 2W - 1 uint32 words (inline records, every substring one 32-bit
 // word).  A stage of records is read in groups of four records (16 (2W - 1)
 // bytes, 16-byte aligned) that start at a multiple of four, and its copy
 // starts up to three records early: it holds the whole groups that fit in
-// kStageBytes, less those three records.
-template <int W, bool REDUCED>
+// SB stage bytes, less those three records.
+template <int W, bool REDUCED, uint32_t SB = kDefaultStageBytes>
 __host__ __device__ constexpr uint32_t stage_entries() {
-    return REDUCED ? 4u * (kStageBytes / (16u * (2 * W - 1))) - 3u : kStageBytes / (8 * W);
+    return REDUCED ? 4u * (SB / (16u * (2 * W - 1))) - 3u : SB / (8 * W);
 }
 
 // Entries per big-bucket slice: 1024 whole codes, or four full stages of
 // records, so that no slice ends in a nearly empty stage.
-template <int W, bool ALIGNED>
+template <int W, bool ALIGNED, uint32_t SB = kDefaultStageBytes>
 __host__ __device__ constexpr uint32_t slice_entries() {
-    return ALIGNED ? 4u * stage_entries<W, true>() : kSliceEntries;
+    return ALIGNED ? 4u * stage_entries<W, true, SB>() : kSliceEntries;
 }
 constexpr uint32_t kScanChunk = 4096;      // codes per chunk of a full verification pass
 constexpr int kQueryShift = 41;            // composite entry: q << 41 | d << 32 | id
@@ -106,6 +106,8 @@ struct SearchArgs {
     uint64_t wait_ns;                  // limit of a bounded wait on stage data
     int wait_test;                     // timeout test: each warp's first wait runs out
     unsigned long long* sliced;        // raw candidates queued as big-bucket slices (nullable)
+    uint32_t slice_entries;            // entries per big-bucket slice (set for the slice kernel's shape)
+    int variant;                       // slice kernel shape (k-NN waves; see kStreamVariants)
 };
 
 // Chunks of step t for a query: ceil(C(s_j, rho) / 256), 0 if rho > s_j.
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_SEARCH_MIN_BLOCKS) search_
     const uint32_t lane = lane_id();
     uint32_t* whist = s_hist[threadIdx.x >> 5];
     const unsigned long long total_chunks = a.chunk_off[a.nq];
-    constexpr uint32_t kSlice = slice_entries<W, ALIGNED>();
+    const uint32_t kSlice = a.slice_entries;
     // Chunk indices: the warp's own index first (no atomic), then nwarps plus
     // the values of a shared counter.  Lane 0 grabs the next index before the
     // current chunk runs and the warp reads it afterwards, so the atomic's round
@@ -844,101 +846,67 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_BIG_MIN_BLOCKS) search_big
 
 // ------------------------------------------------------- streamed slices
 // With inline codes every big-bucket slice is one contiguous run of codes.
-// Each warp streams its slices through a ring of kStages 4 KB shared-memory
-// stages: lane 0 keeps bulk asynchronous copies (cp.async.bulk, completion
-// counted on an mbarrier per stage) of the next kStages - 1 stages in flight
+// Each warp streams its slices through a ring of kStages shared-memory stages
+// (4 KB in the default shape): lane 0 keeps bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier per stage) of the next
+// kStages - 1 stages in flight
 // while the warp verifies the current one.  Every wait on an mbarrier is
 // bounded; on expiry the kernel raises a.timeout, waits (bounded) for its own
 // copies still in flight and leaves.
+// Shapes of the slice kernel: stage bytes, warps per CTA, stages in flight
+// per warp.  The k-NN waves run any of them (mih_tune_search times them on
+// hold-out queries); the collect and count passes run the first.
+template <uint32_t SB, int NW, int NS>
+struct StreamShape {
+    static constexpr uint32_t kStageBytes = SB;
+    static constexpr int kWarps = NW;
+    static constexpr int kStages = NS;
+    static constexpr uint32_t kSlot = SB + 16;   // + one 8-byte code of realignment (W = 1)
+    static constexpr size_t kSmem = static_cast<size_t>(NW) * NS * kSlot;
+    // resident CTAs per SM the stage ring leaves room for (sets the register budget)
+    static constexpr int kMinBlocks = (227 * 1024) / (kSmem + 8 * 1024) > 0 ? (227 * 1024) / (kSmem + 8 * 1024) : 1;
+    static_assert(NS >= 2 && NS <= 4, "stage ring of 2 to 4 slots");
+};
 #ifndef MIH_STREAM_STAGES
 #define MIH_STREAM_STAGES 2
 #endif
 #ifndef MIH_STREAM_WARPS
 #define MIH_STREAM_WARPS 8
 #endif
-constexpr int kStages = MIH_STREAM_STAGES;
-constexpr int kStreamWarps = MIH_STREAM_WARPS;
-static_assert(kStages >= 2 && kStages <= 4, "stage ring of 2 to 4 slots");
-constexpr uint32_t kWaitHintNs = 20000;          // longest suspension of one try_wait
-constexpr uint64_t kWaitNs = 1000000000ull;      // a bulk copy not done after 1 s is an error
-constexpr uint32_t kStageSlot = kStageBytes + 16;   // + one 8-byte code of realignment (W = 1)
+using Shape0 = StreamShape<kDefaultStageBytes, MIH_STREAM_WARPS, MIH_STREAM_STAGES>;   // the default
+using Shape1 = StreamShape<2 * kDefaultStageBytes, 4, 2>;                             // larger stages, fewer warps
+using Shape2 = StreamShape<kDefaultStageBytes, 8, 3>;                                  // a deeper ring
+constexpr int kStreamVariants = 3;
 
 // Largest bulk copy issue_stage makes for one stage: records start up to three
 // entries early (16-byte aligned groups of four), W = 1 codes up to one, and
 // both round the size up to 16 bytes.  Every layout must fit its slot.
-template <int W, bool REDUCED>
+template <int W, bool REDUCED, uint32_t SB>
 constexpr uint32_t max_stage_copy() {
-    return REDUCED ? (((stage_entries<W, true>() + 3u) * 4u * (2 * W - 1) + 15u) & ~15u)
-                   : (W == 1 ? (((stage_entries<1, false>() + 1u) * 8u + 15u) & ~15u)
-                             : stage_entries<W, false>() * 8u * W);
+    return REDUCED ? (((stage_entries<W, true, SB>() + 3u) * 4u * (2 * W - 1) + 15u) & ~15u)
+                   : (W == 1 ? (((stage_entries<1, false, SB>() + 1u) * 8u + 15u) & ~15u)
+                             : stage_entries<W, false, SB>() * 8u * W);
 }
-static_assert(max_stage_copy<1, false>() <= kStageSlot && max_stage_copy<2, false>() <= kStageSlot &&
-                  max_stage_copy<4, false>() <= kStageSlot,
-              "a stage of whole codes overruns its shared-memory slot");
-static_assert(max_stage_copy<1, true>() <= kStageSlot && max_stage_copy<2, true>() <= kStageSlot &&
-                  max_stage_copy<4, true>() <= kStageSlot,
-              "a stage of records overruns its shared-memory slot");
-static_assert(stage_entries<1, true>() >= 32 && stage_entries<2, true>() >= 32 && stage_entries<4, true>() >= 32 &&
-                  stage_entries<4, false>() % 32 == 0,
-              "a stage holds at least a warp row of entries");
 // Groups of four records read by one lane (16-byte shared loads), and the
 // groups a stage can span; every group a lane reads lies inside its slot.
-template <int W>
+template <int W, uint32_t SB>
 constexpr uint32_t stage_groups() {
-    return (3u + stage_entries<W, true>() + 3u) / 4u;
+    return (3u + stage_entries<W, true, SB>() + 3u) / 4u;
 }
-static_assert(stage_groups<1>() * 16u * (2 * 1 - 1) <= kStageSlot && stage_groups<2>() * 16u * (2 * 2 - 1) <= kStageSlot &&
-                  stage_groups<4>() * 16u * (2 * 4 - 1) <= kStageSlot,
-              "record groups of a stage overrun its shared-memory slot");
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+template <uint32_t SB>
+constexpr bool stage_fits_slot() {
+    constexpr uint32_t slot = SB + 16;
+    return max_stage_copy<1, false, SB>() <= slot && max_stage_copy<2, false, SB>() <= slot &&
+           max_stage_copy<4, false, SB>() <= slot && max_stage_copy<1, true, SB>() <= slot &&
+           max_stage_copy<2, true, SB>() <= slot && max_stage_copy<4, true, SB>() <= slot &&
+           stage_groups<1, SB>() * 16u * 1u <= slot && stage_groups<2, SB>() * 16u * 3u <= slot &&
+           stage_groups<4, SB>() * 16u * 7u <= slot && stage_entries<1, true, SB>() >= 32 &&
+           stage_entries<2, true, SB>() >= 32 && stage_entries<4, true, SB>() >= 32 &&
+           stage_entries<4, false, SB>() % 32 == 0;
 }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_to_smem(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits for the phase of `bar` with the given parity.  Each try_wait may
-// suspend the warp (up to kWaitHintNs, woken early when the phase completes)
-// instead of spinning, so waiting warps leave the issue slots to the warps
-// that verify codes.  Gives up after limit_ns of global time, and in any case
-// after a bounded number of polls (each takes at least a few nanoseconds).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    const uint32_t hint = limit_ns < kWaitHintNs ? static_cast<uint32_t>(limit_ns) : kWaitHintNs;
-    const uint64_t max_polls = limit_ns / 4u + 4096u;
-    uint64_t t0 = 0;
-    for (uint64_t it = 0;; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(hint)
-            : "memory");
-        if (ok) return true;
-        if ((it & 7u) == 0) {
-            const uint64_t now = global_ns();
-            if (it == 0) t0 = now;
-            else if (now - t0 > limit_ns) return false;
-        }
-        if (it >= max_polls) return false;
-    }
-}
+static_assert(stage_fits_slot<Shape0::kStageBytes>() && stage_fits_slot<Shape1::kStageBytes>() &&
+                  stage_fits_slot<Shape2::kStageBytes>(),
+              "a stage's copy or its record groups overrun the shared-memory slot");
 
 // One stage: entries [pos, pos + cnt) of a slice ending at `end`, all of
 // query q at step t, with the query's state for verifying them (loaded when
@@ -955,10 +923,10 @@ struct Stage {
     Code<W> g;
 };
 
-template <int W, bool REDUCED>
+template <int W, bool REDUCED, uint32_t SB>
 __device__ __forceinline__ Stage<W> next_stage(const SearchArgs& a, const Stage<W>& st, unsigned int count,
                                                SliceFeed& feed) {
-    constexpr uint32_t kPer = stage_entries<W, REDUCED>();
+    constexpr uint32_t kPer = stage_entries<W, REDUCED, SB>();
     Stage<W> r = st;
     if (!st.valid) return r;
     if (st.pos + st.cnt < st.end) {
@@ -1016,17 +984,12 @@ __device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage
     return shift;
 }
 
-// resident CTAs per SM the stage ring leaves room for (sets the register budget)
-#ifdef MIH_STREAM_MIN_BLOCKS
-constexpr int kStreamMinBlocks = MIH_STREAM_MIN_BLOCKS;
-#else
-constexpr int kStreamMinBlocks = (227 * 1024) / (kStreamWarps * kStages * (kStageBytes + 16) + 8 * 1024) > 0
-                                     ? (227 * 1024) / (kStreamWarps * kStages * (kStageBytes + 16) + 8 * 1024)
-                                     : 1;
-#endif
-
-template <int W, int MODE, bool ALIGNED>
-__global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_stream_kernel(SearchArgs a) {
+template <int W, int MODE, bool ALIGNED, class Shape>
+__global__ void __launch_bounds__(Shape::kWarps * 32, Shape::kMinBlocks) search_stream_kernel(SearchArgs a) {
+    constexpr int kStreamWarps = Shape::kWarps;
+    constexpr int kStages = Shape::kStages;
+    constexpr uint32_t kStageSlot = Shape::kSlot;
+    constexpr uint32_t SB = Shape::kStageBytes;
     // aligned tables (every substring one 32-bit word) keep inline records
     // without their own word; the others keep whole codes
     constexpr bool REDUCED = ALIGNED;
@@ -1069,24 +1032,24 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
     none.bnd = none.hd = 0;
     none.shift = 0;
     // the ring: cur (slot b), then up to kStages - 1 stages already issued
-    Stage<W> cur = next_stage<W, REDUCED>(a, none, count, feed);
+    Stage<W> cur = next_stage<W, REDUCED, SB>(a, none, count, feed);
     if (!cur.valid) return;
     cur.shift = issue_stage<W, REDUCED>(a, cur, slot0, bar0);
-    Stage<W> n1 = next_stage<W, REDUCED>(a, cur, count, feed);
+    Stage<W> n1 = next_stage<W, REDUCED, SB>(a, cur, count, feed);
     if (n1.valid) n1.shift = issue_stage<W, REDUCED>(a, n1, slot0 + kStageSlot, bar0 + 1);
     Stage<W> n2 = n1;
     if constexpr (kStages >= 3) {
-        n2 = next_stage<W, REDUCED>(a, n1, count, feed);
+        n2 = next_stage<W, REDUCED, SB>(a, n1, count, feed);
         if (n2.valid) n2.shift = issue_stage<W, REDUCED>(a, n2, slot0 + 2 * kStageSlot, bar0 + 2);
     }
     Stage<W> n3 = n2;
     if constexpr (kStages >= 4) {
-        n3 = next_stage<W, REDUCED>(a, n2, count, feed);
+        n3 = next_stage<W, REDUCED, SB>(a, n2, count, feed);
         if (n3.valid) n3.shift = issue_stage<W, REDUCED>(a, n3, slot0 + 3 * kStageSlot, bar0 + 3);
     }
     // entries per lane and batch: whole codes, B of them per lane at a time
     // (a 4 KB stage is 1, 2 or 4 batches for W = 4, 2, 1), or records
-    constexpr int kPer = static_cast<int>(stage_entries<W, REDUCED>());
+    constexpr int kPer = static_cast<int>(stage_entries<W, REDUCED, SB>());
     constexpr int B = kPer / 32 < 4 ? kPer / 32 : 4;
     constexpr int R = 2 * W - 1;
     int b = 0;
@@ -1208,7 +1171,7 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
         __syncwarp();
         // the slot just read takes the stage kStages after cur
         const Stage<W>& last = kStages == 2 ? n1 : (kStages == 3 ? n2 : n3);
-        Stage<W> nn = next_stage<W, REDUCED>(a, last, count, feed);
+        Stage<W> nn = next_stage<W, REDUCED, SB>(a, last, count, feed);
         if (nn.valid) nn.shift = issue_stage<W, REDUCED>(a, nn, slot_b, bar_b);
         // histogram and counters go out once the warp leaves this query
         if (!n1.valid || n1.q != cur.q) {
@@ -1235,7 +1198,13 @@ __global__ void __launch_bounds__(kStreamWarps * 32, kStreamMinBlocks) search_st
     }
 }
 
-size_t stream_smem_bytes() { return static_cast<size_t>(kStreamWarps) * kStages * kStageSlot; }
+// Entries per big-bucket slice and launch shape of each slice-kernel variant.
+template <int W, bool ALIGNED>
+uint32_t variant_slice_entries(int v) {
+    if (v == 1) return slice_entries<W, ALIGNED, Shape1::kStageBytes>();
+    if (v == 2) return slice_entries<W, ALIGNED, Shape2::kStageBytes>();
+    return slice_entries<W, ALIGNED, Shape0::kStageBytes>();
+}
 
 // ------------------------------------------------------------ planning
 // Chunk count of each query's step range [t_lo, t_hi].
@@ -1844,22 +1813,32 @@ unsigned grid1(uint64_t n) {
 // queries and the shared-memory attribute run once per kernel, before any
 // launch (and so never while a stream is being captured).
 struct GridCfg {
-    int bps = 0, bps_big = 0, bps_stream = 0;
+    int bps = 0, bps_big = 0, bps_stream[kStreamVariants] = {};
 };
+
+template <int W, int MODE, bool ALIGNED, class Shape>
+mih_status init_stream_cfg(int* bps) {
+    int x = 0;
+    MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED, Shape>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(Shape::kSmem)));
+    MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, search_stream_kernel<W, MODE, ALIGNED, Shape>,
+                                                           Shape::kWarps * 32, Shape::kSmem));
+    *bps = x > 0 ? x : 1;
+    return MIH_OK;
+}
 
 template <int W, int MODE, bool ALIGNED>
 mih_status init_search_cfg(GridCfg* cfg) {
-    int v = 0, w = 0, x = 0;
-    const size_t smem = stream_smem_bytes();
+    int v = 0, w = 0;
     MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, search_kernel<W, MODE, ALIGNED>, kSearchThreads, 0));
     MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, search_big_kernel<W, MODE, ALIGNED>, kSearchThreads,
                                                            0));
-    MIH_CUDA(cudaFuncSetAttribute(search_stream_kernel<W, MODE, ALIGNED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
-    MIH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, search_stream_kernel<W, MODE, ALIGNED>,
-                                                           kStreamWarps * 32, smem));
+    MIH_TRY((init_stream_cfg<W, MODE, ALIGNED, Shape0>(&cfg->bps_stream[0])));
+    if constexpr (MODE == kModeKnn) {
+        MIH_TRY((init_stream_cfg<W, MODE, ALIGNED, Shape1>(&cfg->bps_stream[1])));
+        MIH_TRY((init_stream_cfg<W, MODE, ALIGNED, Shape2>(&cfg->bps_stream[2])));
+    }
     cfg->bps_big = w > 0 ? w : 1;
-    cfg->bps_stream = x > 0 ? x : 1;
     cfg->bps = v > 0 ? v : 1;
     return MIH_OK;
 }
@@ -1888,10 +1867,14 @@ mih_status search_cfg(const GridCfg** out) {
 }
 
 template <int W, int MODE, bool ALIGNED>
-mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStream_t s, bool launch, bool spans) {
+mih_status launch_search_wa(const SearchArgs& a0, const DeviceInfo& dev, cudaStream_t s, bool launch, bool spans) {
     const GridCfg* cfg = nullptr;
     MIH_TRY((search_cfg<W, MODE, ALIGNED>(&cfg)));
     if (!launch) return MIH_OK;
+    // the slice kernel's shape (k-NN waves only) and the slice size it takes
+    SearchArgs a = a0;
+    a.variant = (MODE == kModeKnn && a.inline_codes && a0.variant > 0 && a0.variant < kStreamVariants) ? a0.variant : 0;
+    a.slice_entries = a.inline_codes ? variant_slice_entries<W, ALIGNED>(a.variant) : kSliceEntries;
     {
         KernelSpan ks(s, MIH_PROF_CHUNK, spans);
         search_kernel<W, MODE, ALIGNED><<<dev.sms * cfg->bps, kSearchThreads, 0, s>>>(a);
@@ -1899,8 +1882,17 @@ mih_status launch_search_wa(const SearchArgs& a, const DeviceInfo& dev, cudaStre
     }
     KernelSpan ks(s, MIH_PROF_SLICE, spans);
     if (a.inline_codes) {
-        search_stream_kernel<W, MODE, ALIGNED>
-            <<<dev.sms * cfg->bps_stream, kStreamWarps * 32, stream_smem_bytes(), s>>>(a);
+        const unsigned grid = dev.sms * cfg->bps_stream[a.variant];
+        if constexpr (MODE == kModeKnn) {
+            if (a.variant == 1)
+                search_stream_kernel<W, MODE, ALIGNED, Shape1><<<grid, Shape1::kWarps * 32, Shape1::kSmem, s>>>(a);
+            else if (a.variant == 2)
+                search_stream_kernel<W, MODE, ALIGNED, Shape2><<<grid, Shape2::kWarps * 32, Shape2::kSmem, s>>>(a);
+            else
+                search_stream_kernel<W, MODE, ALIGNED, Shape0><<<grid, Shape0::kWarps * 32, Shape0::kSmem, s>>>(a);
+        } else {
+            search_stream_kernel<W, MODE, ALIGNED, Shape0><<<grid, Shape0::kWarps * 32, Shape0::kSmem, s>>>(a);
+        }
     } else {
         search_big_kernel<W, MODE, ALIGNED><<<dev.sms * cfg->bps_big, kSearchThreads, 0, s>>>(a);
     }
@@ -2007,6 +1999,7 @@ mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t
     a.timeout = p.timeout;
     a.wait_ns = wait_limit_ns();
     a.wait_test = wait_test_expire() ? 1 : 0;
+    a.variant = ix->slice_shape;
     if (in_graph) return launch_search<MODE>(a, ix->W, dev, s);   // events cannot sit in a loop body
     main_kernel_begin(s);
     const mih_status st = launch_search<MODE>(a, ix->W, dev, s, true, true);

@@ -576,6 +576,37 @@ def test_measured_ceilings_are_plausible(gpu_lib):
     assert c["fp8_mma_pairs128_per_s"] == pytest.approx(c["fp8_mma_tflops"] * 1e12 / 256.0)
 
 
+@pytest.mark.parametrize("q,m", [(128, 4), (128, 5), (64, 2), (256, 8)])
+def test_slice_shapes_and_search_tuning(gpu_lib, orc, q, m):
+    """Every shape of the big-bucket slice kernel gives the oracle's answer
+    (m = q/32 streams records, other m whole codes), and mih_tune_search keeps
+    a valid choice that stays exact.  Big buckets: 20 patterns x 2500 copies."""
+    mih = gpu_lib
+    rng = np.random.default_rng(101)
+    pats = synth.uniform_codes(20, q, 102)
+    db = np.concatenate([np.repeat(pats, 2500, axis=0), synth.uniform_codes(20_001, q, 103)])
+    db = db[rng.permutation(len(db))]
+    qs = np.concatenate([perturb(pats[:8], 3, 104), synth.uniform_codes(8, q, 105)])
+    codes, queries = to_dev(db), to_dev(qs)
+    for k in (10, 3000):
+        want_ids, want_dist = orc.knn(db, qs, k)
+        for shape in (0, 1, 2):
+            ix = mih.mih_build(codes, q, m, inline_codes=1, slice_shape=shape)
+            r = mih.mih_knn(ix, queries, k)
+            assert np.array_equal(ids_of(r["ids"]), want_ids), (shape, k)
+            assert np.array_equal(host(r["dist"]), want_dist), (shape, k)
+            ix.free()
+    ix = mih.mih_build(codes, q, m, inline_codes=1)
+    best, table = mih.mih_tune_search(ix, queries, 100)
+    assert best["slice_shape"] in mih.SLICE_SHAPES and len(table) == 9 and all(v > 0 for v in table.values())
+    want_ids, want_dist = orc.knn(db, qs, 100)
+    r = mih.mih_knn(ix, queries, 100)
+    assert np.array_equal(ids_of(r["ids"]), want_ids) and np.array_equal(host(r["dist"]), want_dist)
+    with pytest.raises(mih.MihError):
+        mih.mih_build(codes, q, m, slice_shape=3)
+    ix.free()
+
+
 def test_autotune_picks_a_candidate(gpu_lib, orc):
     """Sec. 6: m chosen by timing the search on hold-out queries."""
     mih = gpu_lib
