@@ -77,7 +77,8 @@ def parse():
     ap.add_argument("--serve-qps", type=float, default=200_000.0, help="offered load of the serving check")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--tail-from", type=int, default=0,
-                    help="step from which k-NN queries run two steps per wave (0 = library default 2m, <0 never)")
+                    help="step from which k-NN queries run two steps per wave (0: chosen by mih_tune_search, "
+                         "or never with --no-autotune; <0 never)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads (1e9 x 64, 1e9 x 256, three-database serving) after the headline")
     ap.add_argument("--opt-substrings", action="store_true",
@@ -349,12 +350,14 @@ def run_ours(a):
     info = index.info()
     # launch choices of the k-NN waves (slice-kernel shape, two-step start),
     # timed on the hold-out queries and kept in the index
+    # (hold-out batch of the benchmark's size: the per-wave overheads that
+    # two-step waves save weigh differently in smaller batches)
     search_tuning = None
     if not a.no_autotune and a.tail_from == 0:
-        hold = make_codes(kind, 1000, q, 5, dev)
+        hold = make_codes(kind, nq, q, 5, dev)
         t0 = time.perf_counter()
         best, table = mih.mih_tune_search(index, hold, k if k != "kper" else 100)
-        search_tuning = {"chosen": best, "ms_per_query": table, "holdout_queries": 1000,
+        search_tuning = {"chosen": best, "ms_per_query": table, "holdout_queries": nq,
                          "seconds": time.perf_counter() - t0}
         del hold
         torch.cuda.empty_cache()
@@ -610,7 +613,7 @@ def run_ours(a):
                    "index_bytes": info["index_bytes"], "build_ms": build_ms, "gen_s": gen_s,
                    "inline_codes": info["inline_codes"], "executor": a.executor, "substrings": substrings,
                    "tail_from": (search_tuning["chosen"]["tail_from"] if search_tuning else
-                                 (a.tail_from if a.tail_from else 2 * m)),
+                                 (a.tail_from if a.tail_from > 0 else "never")),
                    "search_tuning": search_tuning,
                    "autotune": tune},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
@@ -625,9 +628,15 @@ def run_ours(a):
         extra = {}
         for wl, wm in (("3", 3), ("4", 8)):   # the m the autotuner chose for these workloads
             extra[wl] = batch_workload(wl, wm, dev)
+        # the by-id gather against the measured random 32-byte read ceiling
+        bb = extra["4"]["big_bucket_kernel"]
+        if bb["gbs"]:
+            bb["ceiling_gbs"] = ceilings["gather32_gbs"]
+            bb["frac_of_ceiling"] = bb["gbs"] / ceilings["gather32_gbs"]
         dbs, loads = serving_loads(a, dev)
         extra["5"] = {"workload": WORKLOAD_NAMES["5"], "databases": dbs, "loads": loads,
                       "k": "log-uniform[1,1000]", "latency": "arrival to results in host memory"}
+        extra["layouts"] = layout_effect(dev)
         line["extra_workloads"] = extra
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -697,6 +706,29 @@ def run_serving(a):
     print(json.dumps(line), flush=True)
 
 
+def layout_effect(dev, m=5):
+    """Per-table substring lengths at 1e9 x 128-bit, k = 100: the Sec. 2.1 layout
+    against the cost-model layout for the measured stop steps (m = 4 leaves no
+    freedom: four 32-bit substrings), timed by mih_autotune_layout on 10^4
+    hold-out queries."""
+    import torch
+
+    import paper_1307_2982_gb300 as mih
+
+    codes = make_codes("lsh", 1_000_000_000, 128, 0, dev)
+    hold = make_codes("lsh", 10_000, 128, 5, dev)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    lengths, times = mih.mih_autotune_layout(codes, 128, hold, 100, m)
+    out = {"workload": "1B x 128-bit LSH-style codes, 10k hold-out queries, k=100", "m": m,
+           "uniform_lengths": mih.mih_substring_layout(128, m)[1], "chosen_lengths": lengths,
+           "ms_per_query": times, "seconds": time.perf_counter() - t0}
+    del codes, hold
+    torch.cuda.empty_cache()
+    return out
+
+
 def batch_workload(wl, m, dev, steps=3, warmup=3, parity_sample=6, ls_queries=1000):
     """One of the batched 1e9-code workloads at reduced repeats: queries/s of
     mih_knn over 10^4 queries (CUDA events), the linear scan on the first
@@ -723,6 +755,9 @@ def batch_workload(wl, m, dev, steps=3, warmup=3, parity_sample=6, ls_queries=10
     torch.cuda.synchronize()
     build_ms = ev0.elapsed_time(ev1)
     info = index.info()
+    hold = make_codes(kind, nq, q, 5, dev)
+    best, _ = mih.mih_tune_search(index, hold, 100)
+    del hold
     tot = int(kt.sum().item()) if kt is not None else nq * k
     out_ids = torch.empty(tot, dtype=torch.int32, device=dev)
     out_dist = torch.empty(tot, dtype=torch.int32, device=dev)
@@ -738,6 +773,13 @@ def batch_workload(wl, m, dev, steps=3, warmup=3, parity_sample=6, ls_queries=10
     ev1.record()
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / steps
+    # one more batch with an event pair around every kernel (host-loop waves)
+    mih.mih_set_timing(2)
+    rb = mih.mih_knn(index, queries, karg, out=(out_ids, out_dist))
+    prof = mih.mih_last_profile()
+    mih.mih_set_timing(0)
+    kernels_ms = {kk: v for kk, v in prof["kernel_ms"].items() if prof["kernel_launches"][kk]}
+    bstats = rb["stats"]
     off = r.get("offsets")
     off_h = off.cpu().numpy() if off is not None else np.arange(nq + 1, dtype=np.int64) * k
     ids_h = out_ids.cpu().numpy().view(np.uint32)
@@ -777,10 +819,23 @@ def batch_workload(wl, m, dev, steps=3, warmup=3, parity_sample=6, ls_queries=10
     del db_h
     value = nq / (ms / 1000.0)
     ls_qps = ls_queries / (ls_ms / 1000.0)
-    return {"workload": WORKLOAD_NAMES[wl], "m": m, "value": value, "unit": "queries/s", "ms_per_step": ms,
+    # the big-bucket kernel's bytes over its own time: whole codes by id (q/8 B
+    # of code + 4 B of id per candidate) without inline codes, else inline
+    if info["inline_codes"]:
+        cand_b = q // 8 - (4 if m == q // 32 else 0)
+    else:
+        cand_b = q // 8 + 4
+    slice_gbs = (bstats["candidates_sliced"] * cand_b / (kernels_ms["slice"] / 1000.0) / 1e9
+                 if kernels_ms.get("slice") else None)
+    return {"workload": WORKLOAD_NAMES[wl], "m": m, "search_tuning": best, "value": value, "unit": "queries/s",
+            "ms_per_step": ms,
             "steps": steps, "warmup": warmup, "timing": "CUDA events around the batches",
             "build_ms": build_ms, "gen_s": gen_s, "inline_codes": info["inline_codes"],
             "index_bytes": info["index_bytes"], "mih_stats_per_step": {key: v / steps for key, v in stats.items()},
+            "kernels_ms_per_step": kernels_ms,
+            "big_bucket_kernel": {"gbs": slice_gbs, "bytes_model": f"{cand_b} B per candidate of a big bucket",
+                                  "kind": "inline codes, streamed" if info["inline_codes"] else
+                                  "codes gathered by id (random 32-byte sectors)"},
             "linscan": {"queries": ls_queries, "value": ls_qps, "unit": "queries/s", "mih_speedup": value / ls_qps,
                         "identical_to_mih": ls_same, "pairs_per_s": float(n) * ls_queries / (ls_ms / 1000.0)},
             "parity": {"sampled_queries": parity_sample, "mismatched_queries": mism, "reference": "oracle"}}

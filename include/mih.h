@@ -94,8 +94,10 @@ typedef struct {
                               steps 0..t every code within t bits is found,
                               Prop. 2, so the stopping test after a wave stays
                               exact; a query may do one step more than Alg. 3).
-                              Saves waves when few slow queries remain.  0 =
-                              default (step 2m), negative = never.  Never with
+                              Saves waves when few slow queries remain, at the
+                              price of the extra steps' work: whether it pays
+                              depends on the workload (mih_tune_search times it).
+                              0 = default (never), negative = never.  Never with
                               per-query counters requested (they are Alg. 3's). */
     const int32_t *bit_order; /* Sec. 5.5 "Substring Optimization": NULL = the
                               consecutive substrings of Sec. 2.1.  Otherwise a

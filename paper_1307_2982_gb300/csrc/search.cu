@@ -1508,11 +1508,16 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
     }
     const int dk = a.dk[q];
     const uint32_t* h = a.hist + static_cast<uint64_t>(q) * (a.q + 1);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        // codes closer than d_k: the histogram below d_k, summed by warp 0
         unsigned long long below = 0;
-        for (int d = 0; d < dk; ++d) below += h[d];
-        s_below = below;
-        s_n = 0;
+        for (int d = static_cast<int>(threadIdx.x); d < dk; d += 32) below += h[d];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) below += __shfl_down_sync(0xFFFFFFFFu, below, o);
+        if (threadIdx.x == 0) {
+            s_below = below;
+            s_n = 0;
+        }
     }
     __syncthreads();
     const uint32_t ties = h[dk];
@@ -1535,11 +1540,20 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a) {
     const uint64_t within = s_below + ties;
     if (within <= a.smem_entries) {
         // one pass: the entries within d_k, ids resolved, into shared memory
-        for (uint64_t i = threadIdx.x; i < nsrc; i += blockDim.x) {
-            const uint64_t e = src[i];
-            if (static_cast<int>((e & kEntryMask) >> 32) <= dk) {
-                const unsigned int slot = atomicAdd(&s_n, 1u);
-                if (slot < within) res[slot] = resolved_entry(e, tables);
+        // (four loads per thread in flight before any is used)
+        for (uint64_t i0 = threadIdx.x; i0 < nsrc; i0 += 4ull * blockDim.x) {
+            uint64_t e[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const uint64_t i = i0 + static_cast<uint64_t>(r) * blockDim.x;
+                e[r] = i < nsrc ? src[i] : ~0ull;   // ~0: distance field above any d_k
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (static_cast<int>((e[r] & kEntryMask) >> 32) <= dk) {
+                    const unsigned int slot = atomicAdd(&s_n, 1u);
+                    if (slot < within) res[slot] = resolved_entry(e[r], tables);
+                }
             }
         }
         __syncthreads();

@@ -241,8 +241,8 @@ def test_graph_and_host_executors_agree(gpu_lib, orc, kind, q, m, n):
 @pytest.mark.parametrize("kind,q,m,n", [("lsh", 128, 4, 200_003), ("uniform", 64, 3, 80_000),
                                         ("lsh", 256, 9, 60_001), ("ties", 128, 4, 30_000)])
 def test_two_step_waves_keep_results(gpu_lib, orc, kind, q, m, n):
-    """Two Alg. 3 steps per wave (from step 1, or the default step 2m) give the
-    oracle's answer, as one step per wave does, in no more waves."""
+    """Two Alg. 3 steps per wave (from step 1, or from step 2m) give the
+    oracle's answer, as one step per wave (the default) does, in no more waves."""
     import torch
 
     mih = gpu_lib
@@ -251,14 +251,14 @@ def test_two_step_waves_keep_results(gpu_lib, orc, kind, q, m, n):
     ks = synth.per_query_k(257, seed=6, kmax=1000)
     off, wi, wd = orc.knn(db, qs, ks)
     waves = {}
-    for tail in (-1, 1, 0):
+    for tail in (-1, 1, 2 * m, 0):
         ix = mih.mih_build(codes, q, m, tail_from=tail)
         r = mih.mih_knn(ix, queries, torch.from_numpy(ks.astype(np.int32)).cuda())
         assert np.array_equal(ids_of(r["ids"]), wi), tail
         assert np.array_equal(host(r["dist"]), wd), tail
         waves[tail] = r["stats"]["waves"]
         ix.free()
-    assert waves[1] <= waves[-1] and waves[0] <= waves[-1], waves
+    assert waves[1] <= waves[-1] and waves[2 * m] <= waves[-1] and waves[0] == waves[-1], waves
 
 
 def test_reused_wave_graph_across_calls(gpu_lib, orc):
