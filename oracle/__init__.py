@@ -20,6 +20,8 @@ Functions and the passages they follow:
 - ``ring``                 Algorithm 3 (buckets at exactly r' bits)
 - ``MihOracle.knn``        Algorithm 3 (with step counters)
 - ``MihOracle.rnear``      Algorithm 2 (with step counters)
+- ``rerank_asym``          Sec. 5.1 / Conclusion: re-ranking by an asymmetric
+                           Hamming distance (the reading is in the C source)
 
 Every function is pinned by ``tests/test_oracle_pins.py`` to something other
 than itself (numpy brute force, Eq. 1, Propositions 1-2, special cases).
@@ -75,6 +77,8 @@ def _load():
         lib.orc_table_build.restype = i32
         lib.orc_ring.argtypes = [i32, i32, P, u64]
         lib.orc_ring.restype = u64
+        lib.orc_rerank_asym.argtypes = [P, u64, i32, P, u64, P, ctypes.c_uint32, ctypes.c_uint32, P, P]
+        lib.orc_rerank_asym.restype = i32
         lib.orc_mih_knn_flat.argtypes = [i32, i32, P, u64, i32, P, P, P, P, P,
                                          ctypes.c_uint32, P, P, P]
         lib.orc_mih_knn_flat.restype = i32
@@ -143,6 +147,28 @@ def knn(codes, queries, k, nthreads: int | None = None):
     if uniform:
         return ids[:tot].reshape(nq, int(k)), dist[:tot].reshape(nq, int(k))
     return off, ids[:tot], dist[:tot]
+
+
+def rerank_asym(codes, proj, ids, k: int):
+    """(ids[nq][k], a[nq][k]): every row of candidate ids (uint32 [nq][k_in],
+    0xFFFFFFFF = padding) ordered by (asymmetric Hamming distance, id) to the
+    query's real values proj[nq][q] (float32), first k kept, padded with
+    0xFFFFFFFF / -1.0."""
+    codes = _codes(codes)
+    proj = np.ascontiguousarray(proj, dtype=np.float32)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    nq, q = proj.shape
+    if ids.ndim != 2 or ids.shape[0] != nq or q != 64 * codes.shape[1]:
+        raise ValueError("rerank_asym: shapes do not match")
+    out_ids = np.zeros((nq, k), dtype=np.uint32)
+    out_a = np.zeros((nq, k), dtype=np.float64)
+    st = _load().orc_rerank_asym(_ptr(codes), codes.shape[0], q, _ptr(proj), nq, _ptr(ids),
+                                 ids.shape[1], k, _ptr(out_ids), _ptr(out_a))
+    if st == -2:
+        raise ValueError("rerank_asym: candidate id out of range")
+    if st:
+        raise MemoryError("oracle rerank_asym failed")
+    return out_ids, out_a
 
 
 def rnear(codes, queries, r: int, nthreads: int | None = None):

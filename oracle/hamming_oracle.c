@@ -28,6 +28,8 @@
  *   orc_ring             Algorithm 3 (buckets at exactly r' bits), brute force
  *   orc_mih_rnear        Algorithm 2 (r-neighbour search by MIH)
  *   orc_mih_knn          Algorithm 3 (k-NN search by MIH, growing radius)
+ *   orc_rerank_asym      Sec. 5.1 / Conclusion: candidates re-ranked by an
+ *                        asymmetric Hamming distance (reading c17)
  *
  * Parity is pinned by tests/test_oracle_pins.py against brute force in numpy,
  * closed forms (Eq. 1), Propositions 1 and 2, and special cases.
@@ -474,4 +476,66 @@ int64_t orc_mih_rnear_flat(int q, int m, const uint64_t *codes, uint64_t n, int 
 {
     orc_mih X = {q, m, W, codes, n, off, len, keys, ids};
     return orc_mih_rnear(&X, g, r, cap, out_ids, out_dist, cnt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Re-ranking by an asymmetric Hamming distance.  Sec. 5.1 notes that Hamming
+ * distance cannot order codes at equal distance and that a re-ranking phase
+ * with an asymmetric Hamming distance helps in practice; the Conclusion
+ * describes the asymmetric form: the query stays real-valued (no quantisation
+ * of the query), and multi-index hashing supplies the candidates that the
+ * asymmetric distance then culls.  The paper gives no formula.  Reading c17:
+ * the query is the q real values y_b whose signs give its code (bit b is set
+ * when y_b > 0), and the distance to a database code h is
+ *     a(y, h) = sum of |y_b| over the bits b where h_b != [y_b > 0],
+ * every disagreeing bit weighted by the query's margin from that bit's
+ * threshold.  The sum is taken in double precision, bit 0 first.  Each
+ * query's candidate list is ordered by (a, id) and its first k entries are
+ * returned; candidate id 0xFFFFFFFF is padding and is skipped, and result
+ * slots past the candidates are padded with id 0xFFFFFFFF and a = -1.
+ * Returns 0, -1 when out of memory, -2 when a candidate id is >= n. */
+typedef struct {
+    double a;
+    uint32_t id;
+} orc_scored;
+
+static int scored_cmp(const void *x, const void *y)
+{
+    const orc_scored *u = (const orc_scored *)x, *v = (const orc_scored *)y;
+    if (u->a != v->a) return u->a < v->a ? -1 : 1;
+    return (u->id > v->id) - (u->id < v->id);
+}
+
+int orc_rerank_asym(const uint64_t *codes, uint64_t n, int q, const float *proj,
+                    uint64_t nq, const uint32_t *ids, uint32_t k_in, uint32_t k,
+                    uint32_t *out_ids, double *out_a)
+{
+    const int W = q / 64;
+    orc_scored *list = (orc_scored *)malloc(sizeof(orc_scored) * (k_in ? k_in : 1));
+    if (!list) return -1;
+    for (uint64_t qi = 0; qi < nq; ++qi) {
+        const float *y = proj + qi * (uint64_t)q;
+        uint32_t cnt = 0;
+        for (uint32_t i = 0; i < k_in; ++i) {
+            uint32_t id = ids[qi * k_in + i];
+            if (id == ORC_PAD_ID) continue;
+            if ((uint64_t)id >= n) { free(list); return -2; }
+            const uint64_t *h = codes + (uint64_t)id * W;
+            double a = 0.0;
+            for (int b = 0; b < q; ++b) {
+                int query_bit = y[b] > 0.0f;
+                if (code_bit(h, b) != query_bit) a += __builtin_fabs((double)y[b]);
+            }
+            list[cnt].a = a;
+            list[cnt].id = id;
+            ++cnt;
+        }
+        qsort(list, cnt, sizeof(orc_scored), scored_cmp);
+        for (uint32_t p = 0; p < k; ++p) {
+            out_ids[qi * k + p] = p < cnt ? list[p].id : ORC_PAD_ID;
+            out_a[qi * k + p] = p < cnt ? list[p].a : -1.0;
+        }
+    }
+    free(list);
+    return 0;
 }

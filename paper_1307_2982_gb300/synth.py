@@ -11,7 +11,9 @@ not available, so two generators stand in for them (Sec. 5):
 - LSH-style codes: 128-d vectors from a mixture of 1000 isotropic Gaussians
   (centres U[0,255], sigma 20, clipped to [0,255]), mean-centred, then
   binarised by the sign of q random N(0,1) projections (Sec. 5: LSH codes are
-  signs of random projections of mean-centred features).
+  signs of random projections of mean-centred features).  The projections
+  themselves (``lsh_projections``) are the real-valued queries of the
+  asymmetric re-ranking.
 
 Codes are packed little-endian into W = q/64 uint64 words: bit b of a code is
 bit (b % 64) of word (b // 64).  Small databases are drawn with numpy on the
@@ -96,20 +98,38 @@ def _pack_bits(bits: np.ndarray) -> np.ndarray:
 
 def lsh_codes(n: int, q: int, seed: int, chunk: int = 200_000) -> np.ndarray:
     """(n, q/64) uint64 LSH-style codes drawn with numpy (host; n up to ~1e7)."""
+    return lsh_projections(n, q, seed, chunk, keep_proj=False)[0]
+
+
+def lsh_projections(n: int, q: int, seed: int, chunk: int = 200_000, keep_proj: bool = True):
+    """(codes, proj): the codes of lsh_codes(n, q, seed) and the float32
+    projections (n, q) whose signs they are (bit b set where proj[:, b] > 0),
+    the real-valued form of the same vectors."""
     words(q)
     rng = np.random.default_rng(seed)
     centres, P = _centres(), _projection(q)
     mu = training_mean().astype(np.float32)
     out = np.empty((n, q // 64), dtype=np.uint64)
+    proj = np.empty((n, q), dtype=np.float32) if keep_proj else None
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         x = _draw_vectors(rng, e - s, centres) - mu
-        out[s:e] = _pack_bits((x @ P.T) > 0)
-    return out
+        y = x @ P.T
+        out[s:e] = _pack_bits(y > 0)
+        if keep_proj:
+            proj[s:e] = y
+    return out, proj
 
 
 def lsh_codes_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_000_000):
     """(n, q/64) int64 tensor of LSH-style codes drawn with torch on `device`."""
+    return lsh_projections_torch(n, q, seed, device, chunk, keep_proj=False)[0]
+
+
+def lsh_projections_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_000_000,
+                          keep_proj: bool = True):
+    """(codes, proj): the codes of lsh_codes_torch(n, q, seed) and the float32
+    projections (n, q) on `device` whose signs they are."""
     import torch
 
     W = words(q)
@@ -118,6 +138,7 @@ def lsh_codes_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_00
     mu = torch.from_numpy(training_mean().astype(np.float32)).to(device)
     shifts = torch.arange(64, device=device, dtype=torch.int64)
     out = torch.empty((n, W), dtype=torch.int64, device=device)
+    proj = torch.empty((n, q), dtype=torch.float32, device=device) if keep_proj else None
     for c, s in enumerate(range(0, n, chunk)):
         e = min(n, s + chunk)
         g = torch.Generator(device=device)
@@ -125,12 +146,16 @@ def lsh_codes_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_00
         idx = torch.randint(0, N_CENTRES, (e - s,), device=device, generator=g)
         x = torch.randn((e - s, DIM), device=device, generator=g)
         x.mul_(SIGMA).add_(centres[idx]).clamp_(0.0, 255.0).sub_(mu)
-        bits = (x @ P.T) > 0
+        y = x @ P.T
         del x
+        bits = y > 0
+        if keep_proj:
+            proj[s:e] = y
+        del y
         b = bits.view(e - s, W, 64).to(torch.int64)
         out[s:e] = (b << shifts).sum(dim=2)
         del bits, b
-    return out
+    return out, proj
 
 
 # ------------------------------------------------------------------ queries

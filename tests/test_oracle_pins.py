@@ -412,3 +412,125 @@ def test_generators_seeded():
     assert ks.min() >= 1 and ks.max() <= 1000
     assert abs(np.median(np.log(ks)) - np.log(1001) / 2) < 0.2
     _ = floor  # noqa
+
+
+# ------------------------------------------- asymmetric re-ranking (reading c17)
+PAD = 0xFFFFFFFF
+
+
+def _rerank_inputs(q, nq, n, k_in, seed):
+    rng = np.random.default_rng(seed)
+    codes = synth.uniform_codes(n, q, seed)
+    ids = np.stack([rng.choice(n, size=k_in, replace=False) for _ in range(nq)]).astype(np.uint32)
+    return rng, codes, ids
+
+
+def _expected_rerank(codes, y, ids, k, weights):
+    """Brute force: disagreement bits of each candidate against the query's
+    sign bits, dotted with `weights` (exact integers here), lexsort by
+    (distance, id)."""
+    bits = unpack(codes)
+    out_ids = np.full((len(ids), k), PAD, dtype=np.uint32)
+    out_a = np.full((len(ids), k), -1.0)
+    for i, row in enumerate(ids):
+        valid = row[row != PAD].astype(np.int64)
+        dis = bits[valid] != (y[i] > 0)[None, :]
+        a = dis.astype(np.int64) @ weights
+        order = np.lexsort((valid, a))[:k]
+        out_ids[i, : len(order)] = valid[order]
+        out_a[i, : len(order)] = a[order]
+    return out_ids, out_a
+
+
+@pytest.mark.parametrize("q", [64, 128, 256])
+def test_rerank_asym_integer_weights(orc, q):
+    """|y_b| = b + 1 with random signs: every partial sum is an exact integer,
+    so the distance equals the integer dot product of the disagreement bits
+    with (1, ..., q) -- a wrong bit index, sign test or dropped term changes
+    it -- and the order is numpy's lexsort of (distance, id).  Row 0 has
+    padding inside it and fewer valid candidates than k."""
+    rng, codes, ids = _rerank_inputs(q, 6, 300, 40, q)
+    ids[0, 7:12] = PAD
+    y = (rng.choice([-1.0, 1.0], size=(6, q)) * np.arange(1, q + 1)).astype(np.float32)
+    k = 38
+    got_ids, got_a = orc.rerank_asym(codes, y, ids, k)
+    exp_ids, exp_a = _expected_rerank(codes, y, ids, k, np.arange(1, q + 1, dtype=np.int64))
+    assert np.array_equal(got_ids, exp_ids)
+    assert np.array_equal(got_a, exp_a)
+    assert (got_ids[0, 35:] == PAD).all() and (got_a[0, 35:] == -1.0).all()
+
+
+def test_rerank_asym_unit_weights_is_hamming_knn(orc):
+    """|y_b| = 1: the asymmetric distance is the Hamming distance to the
+    query's sign code, so the re-ranked list is the k-NN (Sec. 1.1) of that
+    code among the candidates, as the brute-force k-NN gives it."""
+    q, k = 128, 25
+    rng, codes, ids = _rerank_inputs(q, 4, 500, 60, 11)
+    y = rng.choice([-1.0, 1.0], size=(4, q)).astype(np.float32)
+    got_ids, got_a = orc.rerank_asym(codes, y, ids, k)
+    for i in range(4):
+        cand = np.sort(ids[i].astype(np.int64))
+        g = np.packbits((y[i] > 0).astype(np.uint8), bitorder="little").view(np.uint64)
+        loc, dist = bf_knn(codes[cand], g, k)
+        assert np.array_equal(got_ids[i], cand[loc.astype(np.int64)])
+        assert np.array_equal(got_a[i], dist.astype(np.float64))
+
+
+@pytest.mark.parametrize("q", [64, 256])
+def test_rerank_asym_real_projections(orc, q):
+    """Real projections (the LSH generator's): the distance agrees with a
+    float64 matrix product of the disagreement bits with |y| to rounding, the
+    list is sorted by (distance, id) and holds exactly the row's candidates."""
+    codes, _ = synth.lsh_projections(2000, q, 21)
+    _, y = synth.lsh_projections(5, q, 22)
+    rng = np.random.default_rng(3)
+    ids = np.stack([rng.choice(2000, size=300, replace=False) for _ in range(5)]).astype(np.uint32)
+    got_ids, got_a = orc.rerank_asym(codes, y, ids, 300)
+    bits = unpack(codes)
+    for i in range(5):
+        assert np.array_equal(np.sort(got_ids[i]), np.sort(ids[i]))
+        dis = bits[got_ids[i].astype(np.int64)] != (y[i] > 0)[None, :]
+        ref = dis.astype(np.float64) @ np.abs(y[i].astype(np.float64))
+        np.testing.assert_allclose(got_a[i], ref, rtol=1e-12, atol=0)
+        key = np.lexsort((got_ids[i], got_a[i]))
+        assert np.array_equal(key, np.arange(300))
+
+
+def test_rerank_asym_sign_flip_invariance(orc):
+    """Negating y_b and flipping bit b of every code leaves each disagreement,
+    each |y_b| and so each sum unchanged, bit for bit."""
+    q = 128
+    codes, _ = synth.lsh_projections(1000, q, 31)
+    _, y = synth.lsh_projections(3, q, 32)
+    rng = np.random.default_rng(4)
+    ids = np.stack([rng.choice(1000, size=200, replace=False) for _ in range(3)]).astype(np.uint32)
+    flip = rng.random(q) < 0.5
+    mask = np.packbits(flip.astype(np.uint8), bitorder="little").view(np.uint64)
+    y2 = np.where(flip[None, :], -y, y).astype(np.float32)
+    a_ids, a_a = orc.rerank_asym(codes, y, ids, 50)
+    b_ids, b_a = orc.rerank_asym(codes ^ mask[None, :], y2, ids, 50)
+    assert np.array_equal(a_ids, b_ids) and np.array_equal(a_a, b_a)
+
+
+def test_rerank_asym_edges(orc):
+    codes = synth.uniform_codes(10, 64, 1)
+    y = np.ones((2, 64), dtype=np.float32)
+    all_pad = np.full((2, 3), PAD, dtype=np.uint32)
+    ids, a = orc.rerank_asym(codes, y, all_pad, 4)
+    assert (ids == PAD).all() and (a == -1.0).all()
+    with pytest.raises(ValueError):
+        orc.rerank_asym(codes, y, np.array([[1, 10], [2, 3]], dtype=np.uint32), 2)
+    # zero weights add nothing: with y_5 = 2.5 (query bit 5 set) and every
+    # other y_b = 0, a code scores 2.5 exactly when its bit 5 is clear
+    y0 = np.zeros((1, 64), dtype=np.float32)
+    y0[0, 5] = 2.5
+    ids, a = orc.rerank_asym(codes, y0, np.arange(10, dtype=np.uint32)[None, :], 10)
+    clear5 = ((codes[:, 0] >> np.uint64(5)) & np.uint64(1)) == 0
+    assert np.array_equal(a[0][np.argsort(ids[0])], np.where(clear5, 2.5, 0.0))
+
+
+def test_lsh_projections_are_the_codes_signs():
+    codes, proj = synth.lsh_projections(500, 128, 9)
+    assert np.array_equal(codes, synth.lsh_codes(500, 128, 9))
+    packed = np.packbits((proj > 0).astype(np.uint8), axis=1, bitorder="little").view(np.uint64)
+    assert np.array_equal(packed, codes)
