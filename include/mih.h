@@ -296,6 +296,38 @@ MIH_API mih_status mih_merge_topk(const uint32_t *ids, const int32_t *dist, uint
                                   int32_t *out_dist, void *stream);
 
 /* ------------------------------------------------------------------------
+ * mih_rerank_asym -- the re-ranking phase of Sec. 5.1 with an asymmetric
+ * Hamming distance (the Conclusion: the query stays real-valued; multi-index
+ * hashing finds the candidates, the asymmetric distance culls them).  For
+ * query row i with real projections y = proj[i] (its code is their signs:
+ * bit b set where y_b > 0) and database code h,
+ *     a(y, h) = sum of |y_b| over the bits b where h_b != [y_b > 0],
+ * accumulated in fp64 in increasing b (so the value is one fixed IEEE
+ * number).  Row i's candidates are ordered by (a, id) and the first k kept.
+ * Leaves the exact-Hamming contract of mih_knn: with every |y_b| equal it
+ * orders by Hamming distance, otherwise by the weighted form.
+ *
+ * codes      device, uint64[n][q/64] (as mih_build), read by candidate id;
+ *            16-byte aligned for q >= 128.
+ * n          number of codes, n < 2^32 - 1.  q: 64, 128 or 256.
+ * proj       device, float32[nq][q], row-major; finite values.
+ * ids        device, uint32[nq][k_in]: each row's candidates (e.g. mih_knn's
+ *            out_ids for k_uniform = k_in); 0xFFFFFFFF is padding and is
+ *            skipped; a row may hold any ids below n (duplicates are scored
+ *            as given).
+ * k_in, k    1 <= k_in, k <= MIH_MAX_K.
+ * out_ids    device, uint32[nq][k]: the ids in (a, id) order, then
+ *            0xFFFFFFFF padding when a row has fewer than k candidates.
+ * out_a      device, double[nq][k]: the matching a, -1 for padding.
+ * Synchronises `stream`.
+ * Errors: MIH_EINVAL (sizes, pointers, a candidate id >= n that is not
+ * padding: out_ids / out_a are then unspecified), MIH_ENOMEM, MIH_ECUDA.
+ */
+MIH_API mih_status mih_rerank_asym(const uint64_t *codes, uint64_t n, int q, const float *proj, uint32_t nq,
+                                   const uint32_t *ids, uint32_t k_in, uint32_t k, uint32_t *out_ids,
+                                   double *out_a, void *stream);
+
+/* ------------------------------------------------------------------------
  * mih_set_scan_kernel -- which kernel linscan_knn uses for calls from the
  * calling host thread (results are identical):
  *   MIH_SCAN_POPC    xor and population count per 32-bit word (Sec. 6
@@ -479,9 +511,10 @@ MIH_API mih_status mih_bit_correlation(const uint64_t *codes, uint64_t n, int q,
 
 /* ------------------------------------------------------------------------
  * Per-call profile of the calling host thread (not part of the paper).
- * With timing enabled, mih_knn, mih_rnear and linscan_knn record CUDA events
- * on their stream around their main kernels (the fused search kernels, the
- * linear-scan kernel) and around the whole call.  With per-kernel timing
+ * With timing enabled, mih_knn, mih_rnear, linscan_knn and mih_rerank_asym
+ * record CUDA events on their stream around their main kernels (the fused
+ * search kernels, the linear-scan kernel, the re-ranking kernel) and around
+ * the whole call.  With per-kernel timing
  * (level 2) they also record an event pair around every launch of the kinds
  * below, and mih_knn runs its waves from a host loop (MIH_EXEC_HOST: the
  * same kernels and results, but each launch can be bracketed by events).
@@ -494,7 +527,8 @@ enum {
     MIH_PROF_STOP = 4,      /* knn_stop_kernel: the stopping test of Alg. 3 */
     MIH_PROF_SELECT = 5,    /* select_kernel (with the ids of table positions) */
     MIH_PROF_SCAN = 6,      /* linscan_kernel */
-    MIH_PROF_KINDS = 7
+    MIH_PROF_RERANK = 7,    /* rerank_asym_kernel */
+    MIH_PROF_KINDS = 8
 };
 
 typedef struct {
@@ -510,7 +544,8 @@ typedef struct {
  * call, 2 also every kernel kind above (and host-loop waves in mih_knn). */
 MIH_API void mih_set_timing(int level);
 
-/* Profile of this thread's last mih_knn / mih_rnear / linscan_knn call. */
+/* Profile of this thread's last mih_knn / mih_rnear / linscan_knn /
+ * mih_rerank_asym call. */
 MIH_API mih_status mih_last_profile(mih_profile *out);
 
 /* ------------------------------------------------------------------------

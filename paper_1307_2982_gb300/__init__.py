@@ -37,7 +37,7 @@ EXPORTS = (
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
     "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation", "mih_set_wait_limit",
     "mih_cost_layout", "mih_autotune_layout", "mih_merge_topk", "mih_measure_ceilings",
-    "mih_set_scan_kernel", "mih_k_offsets", "mih_tune_search",
+    "mih_set_scan_kernel", "mih_k_offsets", "mih_tune_search", "mih_rerank_asym",
 )
 
 
@@ -65,7 +65,7 @@ class mih_stats(ctypes.Structure):
 
 
 # mih_profile.kernel_ms / kernel_launches index (MIH_PROF_* in include/mih.h)
-PROF_KINDS = ("chunk", "slice", "probe", "plan", "stop", "select", "scan")
+PROF_KINDS = ("chunk", "slice", "probe", "plan", "stop", "select", "scan", "rerank")
 
 
 class mih_profile(ctypes.Structure):
@@ -145,6 +145,8 @@ def load():
     lib.mih_measure_ceilings.restype = st
     lib.mih_merge_topk.argtypes = [P, P, u32, u32, u32, P, u32, P, P, P]
     lib.mih_merge_topk.restype = st
+    lib.mih_rerank_asym.argtypes = [P, u64, i32, P, u32, P, u32, u32, P, P, P]
+    lib.mih_rerank_asym.restype = st
     lib.mih_suggest_m.argtypes = [i32, u64]
     lib.mih_suggest_m.restype = i32
     lib.mih_status_str.argtypes = [st]
@@ -539,6 +541,38 @@ def mih_merge_topk(ids, dist, id_base, k: int, stream=None, out=None):
     _check(load().mih_merge_topk(_ptr(ids), _ptr(dist), parts, nq, k_in, base.ctypes.data, k, _ptr(oi), _ptr(od),
                                  _stream(stream)), "mih_merge_topk")
     return {"ids": oi, "dist": od}
+
+
+def mih_rerank_asym(codes, q: int, proj, ids, k: int, stream=None, out=None):
+    """Re-rank each row of candidate ids (nq, k_in) CUDA int32 (bit patterns of
+    uint32; -1 = padding) by the asymmetric Hamming distance to the query's
+    real projections proj (nq, q) float32 CUDA.  Returns {"ids": (nq, k)
+    int32, "a": (nq, k) float64}."""
+    import torch
+
+    cptr, n = _codes_arg(codes, q)
+    if not (proj.is_cuda and ids.is_cuda):
+        raise ValueError("proj and ids must be CUDA tensors")
+    if proj.dtype != torch.float32 or proj.dim() != 2 or proj.shape[1] != q or not proj.is_contiguous():
+        raise ValueError(f"proj must be a contiguous (nq, {q}) float32 tensor")
+    if ids.dim() != 2 or ids.shape[0] != proj.shape[0] or ids.element_size() != 4 or not ids.is_contiguous():
+        raise ValueError("ids must be a contiguous (nq, k_in) tensor of 4-byte ids")
+    nq, k_in = ids.shape
+    if out is None:
+        oi = torch.empty((nq, k), dtype=torch.int32, device=ids.device)
+        oa = torch.empty((nq, k), dtype=torch.float64, device=ids.device)
+    else:
+        oi, oa = out
+    _check(load().mih_rerank_asym(cptr, n, q, _ptr(proj), nq, _ptr(ids), k_in, k, _ptr(oi), _ptr(oa),
+                                  _stream(stream)), "mih_rerank_asym")
+    return {"ids": oi, "a": oa}
+
+
+def mih_knn_asym(index, codes, queries, proj, k: int, k_candidates: int, stream=None):
+    """The Hamming k_candidates-NN of each query by mih_knn, re-ranked by
+    mih_rerank_asym to k results: the two calls in sequence."""
+    r = mih_knn(index, queries, k_candidates, stream=stream)
+    return mih_rerank_asym(codes, index.q, proj, r["ids"], k, stream=stream)
 
 
 def linscan_knn_noalloc(codes, q: int, queries, k: int, stream=None, out=None):

@@ -1,0 +1,200 @@
+// rerank.cu -- re-ranking of candidate lists by an asymmetric Hamming
+// distance.  Sec. 5.1 notes that Hamming distance leaves equidistant codes
+// unordered and that a re-ranking phase with an asymmetric Hamming distance
+// helps; the Conclusion describes it: the query stays real-valued, multi-index
+// hashing supplies the candidates and the asymmetric distance culls them.
+// The distance (the paper gives no formula) is
+//     a(y, h) = sum of |y_b| over the bits b where h_b != [y_b > 0],
+// with y the query's q real projections (their signs are its code).  It is
+// accumulated in fp64, bit 0 first, so the result is one fixed IEEE value.
+//
+// One CTA per query row: the row's |y_b| and sign code go to shared memory,
+// every thread scores candidates (a 16- or 32-byte code gathered by id, then
+// one fp64 add per disagreeing bit, visited in increasing bit order), and a
+// bitonic network over the row sorts the (a, id) pairs in shared memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "launch.h"
+#include "mih_internal.cuh"
+
+namespace mih {
+namespace {
+
+struct RerankArgs {
+    const uint64_t* codes;
+    uint64_t n;
+    const float* proj;    // [nq][64 W]
+    const uint32_t* ids;  // [nq][k_in]
+    uint32_t k_in, k, P;  // P: power of two >= k_in, the sort width
+    uint32_t* out_ids;    // [nq][k]
+    double* out_a;
+    unsigned int* bad;    // set when a candidate id is >= n
+};
+
+// Shared memory of a row: sort keys (the bit patterns of the nonnegative
+// fp64 sums, which order like the sums), the sign code, ids, |y_b|.
+template <int W>
+constexpr size_t rerank_smem_bytes(uint32_t P) {
+    return static_cast<size_t>(P) * 12 + W * 8 + W * 64 * 4;
+}
+
+template <int W>
+__global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t* key = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* qcode = key + a.P;
+    uint32_t* cid = reinterpret_cast<uint32_t*>(qcode + W);
+    float* wy = reinterpret_cast<float*>(cid + a.P);
+
+    const uint64_t row = blockIdx.x;
+    const float* y = a.proj + row * (64 * W);
+    for (int b = threadIdx.x; b < 64 * W; b += blockDim.x) wy[b] = fabsf(__ldg(y + b));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    for (int w32 = warp; w32 < 2 * W; w32 += warps) {
+        const unsigned bits = __ballot_sync(0xffffffffu, __ldg(y + w32 * 32 + lane) > 0.f);
+        if (lane == 0) reinterpret_cast<uint32_t*>(qcode)[w32] = bits;   // little-endian words
+    }
+    __syncthreads();
+
+    Code<W> g;
+#pragma unroll
+    for (int w = 0; w < W; ++w) g.w[w] = qcode[w];
+    for (uint32_t i = threadIdx.x; i < a.P; i += blockDim.x) {
+        uint64_t kk = ~0ull;
+        uint32_t id = kPadId;
+        if (i < a.k_in) {
+            id = __ldg(a.ids + row * a.k_in + i);
+            if (id != kPadId && id >= a.n) {
+                atomicOr(a.bad, 1u);
+                id = kPadId;
+            }
+            if (id != kPadId) {
+                const Code<W> h = load_code<W>(a.codes, id);
+                double s = 0.0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    uint64_t x = h.w[w] ^ g.w[w];
+                    while (x) {
+                        const int b = __ffsll(static_cast<long long>(x)) - 1;
+                        s = __dadd_rn(s, static_cast<double>(wy[64 * w + b]));
+                        x &= x - 1;
+                    }
+                }
+                kk = static_cast<uint64_t>(__double_as_longlong(s));
+            }
+        }
+        key[i] = kk;
+        cid[i] = id;
+    }
+
+    // bitonic sort of (key, id), ascending; padding (key ~0, id ~0) goes last
+    for (uint32_t size = 2; size <= a.P; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (uint32_t t = threadIdx.x; t < a.P / 2; t += blockDim.x) {
+                const uint32_t lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const uint64_t kl = key[lo], kh = key[hi];
+                const uint32_t il = cid[lo], ih = cid[hi];
+                const bool greater = kl > kh || (kl == kh && il > ih);
+                if (greater == ((lo & size) == 0)) {
+                    key[lo] = kh;
+                    key[hi] = kl;
+                    cid[lo] = ih;
+                    cid[hi] = il;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    for (uint32_t p = threadIdx.x; p < a.k; p += blockDim.x) {
+        const bool real = p < a.P && key[p] != ~0ull;
+        a.out_ids[row * a.k + p] = real ? cid[p] : kPadId;
+        a.out_a[row * a.k + p] = real ? __longlong_as_double(static_cast<long long>(key[p])) : -1.0;
+    }
+}
+
+template <int W>
+mih_status launch_rerank(const RerankArgs& a, uint32_t nq, cudaStream_t s) {
+    const size_t smem = rerank_smem_bytes<W>(a.P);
+    if (smem > 48 * 1024)
+        MIH_CUDA(cudaFuncSetAttribute(rerank_asym_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+    const unsigned threads = std::min<unsigned>(512u, std::max<unsigned>(64u, a.P));
+    main_kernel_begin(s);
+    {
+        KernelSpan span(s, MIH_PROF_RERANK);
+        rerank_asym_kernel<W><<<nq, threads, smem, s>>>(a);
+    }
+    main_kernel_end(s);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
+}  // namespace
+}  // namespace mih
+
+extern "C" mih_status mih_rerank_asym(const uint64_t* codes, uint64_t n, int q, const float* proj, uint32_t nq,
+                                      const uint32_t* ids, uint32_t k_in, uint32_t k, uint32_t* out_ids,
+                                      double* out_a, void* stream) {
+    using namespace mih;
+    clear_error();
+    if (q != 64 && q != 128 && q != 256) {
+        set_error("mih_rerank_asym: q must be 64, 128 or 256 (got %d)", q);
+        return MIH_EINVAL;
+    }
+    if (n >= 0xFFFFFFFFull) {
+        set_error("mih_rerank_asym: n must be below 2^32 - 1");
+        return MIH_EINVAL;
+    }
+    if (k_in < 1 || k_in > MIH_MAX_K || k < 1 || k > MIH_MAX_K) {
+        set_error("mih_rerank_asym: k_in and k must be in [1, %u]", MIH_MAX_K);
+        return MIH_EINVAL;
+    }
+    if (nq > (1u << 23)) {
+        set_error("mih_rerank_asym: nq must be at most 2^23");
+        return MIH_EINVAL;
+    }
+    if (nq == 0) return MIH_OK;
+    const int W = q / 64;
+    if (n > 0) {
+        MIH_TRY(check_device_ptr(codes, "mih_rerank_asym: codes"));
+        MIH_TRY(check_code_alignment(codes, W, "mih_rerank_asym: codes"));
+    }
+    MIH_TRY(check_device_ptr(proj, "mih_rerank_asym: proj"));
+    MIH_TRY(check_device_ptr(ids, "mih_rerank_asym: ids"));
+    MIH_TRY(check_device_ptr(out_ids, "mih_rerank_asym: out_ids"));
+    MIH_TRY(check_device_ptr(out_a, "mih_rerank_asym: out_a"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CallScope scope(s);
+    Workspace ws(s);
+    unsigned int* bad;
+    MIH_TRY(ws.alloc(&bad, 1));
+    MIH_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), s));
+
+    RerankArgs a;
+    a.codes = codes;
+    a.n = n;
+    a.proj = proj;
+    a.ids = ids;
+    a.k_in = k_in;
+    a.k = k;
+    a.P = 2;
+    while (a.P < k_in) a.P <<= 1;
+    a.out_ids = out_ids;
+    a.out_a = out_a;
+    a.bad = bad;
+    if (W == 1) MIH_TRY(launch_rerank<1>(a, nq, s));
+    else if (W == 2) MIH_TRY(launch_rerank<2>(a, nq, s));
+    else MIH_TRY(launch_rerank<4>(a, nq, s));
+    unsigned int hbad = 0;
+    MIH_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    MIH_CUDA(cudaStreamSynchronize(s));
+    if (hbad) {
+        set_error("mih_rerank_asym: a candidate id is >= n (0xFFFFFFFF is the only padding id)");
+        return MIH_EINVAL;
+    }
+    return MIH_OK;
+}

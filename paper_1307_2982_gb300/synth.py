@@ -123,13 +123,22 @@ def lsh_projections(n: int, q: int, seed: int, chunk: int = 200_000, keep_proj: 
 
 def lsh_codes_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_000_000):
     """(n, q/64) int64 tensor of LSH-style codes drawn with torch on `device`."""
-    return lsh_projections_torch(n, q, seed, device, chunk, keep_proj=False)[0]
+    return _lsh_torch(n, q, seed, device, chunk, False, False)[0]
 
 
-def lsh_projections_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_000_000,
-                          keep_proj: bool = True):
+def lsh_projections_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_000_000):
     """(codes, proj): the codes of lsh_codes_torch(n, q, seed) and the float32
     projections (n, q) on `device` whose signs they are."""
+    return _lsh_torch(n, q, seed, device, chunk, True, False)[:2]
+
+
+def lsh_vectors_torch(n: int, q: int, seed: int, device="cuda", chunk: int = 10_000_000):
+    """(codes, proj, x): as lsh_projections_torch, plus the mean-centred
+    128-d float32 vectors x the projections were taken of."""
+    return _lsh_torch(n, q, seed, device, chunk, True, True)
+
+
+def _lsh_torch(n, q, seed, device, chunk, keep_proj, keep_x):
     import torch
 
     W = words(q)
@@ -139,6 +148,7 @@ def lsh_projections_torch(n: int, q: int, seed: int, device="cuda", chunk: int =
     shifts = torch.arange(64, device=device, dtype=torch.int64)
     out = torch.empty((n, W), dtype=torch.int64, device=device)
     proj = torch.empty((n, q), dtype=torch.float32, device=device) if keep_proj else None
+    xs = torch.empty((n, DIM), dtype=torch.float32, device=device) if keep_x else None
     for c, s in enumerate(range(0, n, chunk)):
         e = min(n, s + chunk)
         g = torch.Generator(device=device)
@@ -147,6 +157,8 @@ def lsh_projections_torch(n: int, q: int, seed: int, device="cuda", chunk: int =
         x = torch.randn((e - s, DIM), device=device, generator=g)
         x.mul_(SIGMA).add_(centres[idx]).clamp_(0.0, 255.0).sub_(mu)
         y = x @ P.T
+        if keep_x:
+            xs[s:e] = x
         del x
         bits = y > 0
         if keep_proj:
@@ -155,7 +167,7 @@ def lsh_projections_torch(n: int, q: int, seed: int, device="cuda", chunk: int =
         b = bits.view(e - s, W, 64).to(torch.int64)
         out[s:e] = (b << shifts).sum(dim=2)
         del bits, b
-    return out, proj
+    return out, proj, xs
 
 
 # ------------------------------------------------------------------ queries

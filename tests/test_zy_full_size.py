@@ -6,7 +6,9 @@ the other GPU tests (a minute or two per case: generation, build, and the
 oracle's pass over up to 32 GB of codes).
 
 Configurations:
-- 1e9 x 128-bit LSH-style codes, k = 100, m = 4 (inline records);
+- 1e9 x 128-bit LSH-style codes, k = 100, m = 4 (inline records); the
+  batch's 100-NN lists are also re-ranked to 10 by the asymmetric distance
+  (mih_rerank_asym) and checked against the oracle's re-ranking;
 - 1e9 x 64-bit uniform codes, per-query k log-uniform in [1, 1000], m = 3;
 - 1e9 x 256-bit LSH-style codes, per-query k log-uniform in [1, 1000], m = 9:
   the index keeps no inline codes (they would need 9 x 32 GB), so every
@@ -58,6 +60,15 @@ def test_full_size_sampled_parity(gpu_lib, orc, kind, q, n, m, k, sample, inline
         ids_all, dist_all = r["ids"].cpu().numpy().view(np.uint32), r["dist"].cpu().numpy()
         got = [(ids_all[i], dist_all[i]) for i in rows]
         ksample = k
+    rerank = None
+    if kind == "lsh" and q == 128 and k == 100:
+        # the re-ranking phase on the whole batch: 100 Hamming neighbours of
+        # every query re-ranked to 10 by the asymmetric distance
+        _, proj = synth.lsh_projections_torch(NQ, q, 1, device=dev)
+        rr = mih.mih_rerank_asym(codes, q, proj, r["ids"], 10)
+        rerank = (proj[torch.from_numpy(rows).to(dev)].cpu().numpy(),
+                  rr["ids"].cpu().numpy().view(np.uint32)[rows], rr["a"].cpu().numpy()[rows])
+        del proj, rr
     qsel = queries[torch.from_numpy(rows).to(dev)].contiguous()
     ls = mih.linscan_knn(codes, q, qsel, torch.from_numpy(np.asarray(ksample, dtype=np.int32)).to(dev)
                          if k == "kper" else k)
@@ -84,4 +95,7 @@ def test_full_size_sampled_parity(gpu_lib, orc, kind, q, n, m, k, sample, inline
         assert not bad, bad[:10]
         assert np.array_equal(ls["ids"].cpu().numpy().view(np.uint32), wids)
         assert np.array_equal(ls["dist"].cpu().numpy(), wdist)
+        if rerank is not None:
+            want_ids, want_a = orc.rerank_asym(db, rerank[0], wids, 10)
+            assert np.array_equal(rerank[1], want_ids) and np.array_equal(rerank[2], want_a)
     del db
