@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
     ):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp]
+            ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp, "-lm"]
         )
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -34,6 +34,7 @@
  * Parity is pinned by tests/test_oracle_pins.py against brute force in numpy,
  * closed forms (Eq. 1), Propositions 1 and 2, and special cases.
  */
+#include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -489,13 +490,17 @@ int64_t orc_mih_rnear_flat(int q, int m, const uint64_t *codes, uint64_t n, int 
  * when y_b > 0), and the distance to a database code h is
  *     a(y, h) = sum of |y_b| over the bits b where h_b != [y_b > 0],
  * every disagreeing bit weighted by the query's margin from that bit's
- * threshold.  The sum is taken in double precision, bit 0 first.  Each
- * query's candidate list is ordered by (a, id) and its first k entries are
- * returned; candidate id 0xFFFFFFFF is padding and is skipped, and result
- * slots past the candidates are padded with id 0xFFFFFFFF and a = -1.
+ * threshold.  The sum is exact on a fixed-point grid: with M the largest
+ * |y_b| of the query and E its binary exponent (2^E <= M < 2^(E+1)), the
+ * weights are w_b = floor(|y_b| 2^s) with s = 53 - E (each below 2^54), their
+ * sum over the disagreeing bits is an exact integer (below 2^62, any order),
+ * and a = that integer rounded to double, times 2^-s.  Each query's candidate
+ * list is ordered by (integer sum, id) and its first k entries are returned;
+ * candidate id 0xFFFFFFFF is padding and is skipped, and result slots past
+ * the candidates are padded with id 0xFFFFFFFF and a = -1.
  * Returns 0, -1 when out of memory, -2 when a candidate id is >= n. */
 typedef struct {
-    double a;
+    uint64_t a;
     uint32_t id;
 } orc_scored;
 
@@ -515,16 +520,29 @@ int orc_rerank_asym(const uint64_t *codes, uint64_t n, int q, const float *proj,
     if (!list) return -1;
     for (uint64_t qi = 0; qi < nq; ++qi) {
         const float *y = proj + qi * (uint64_t)q;
+        /* the grid: s = 53 - E for the largest magnitude M = m 2^e, m in [0.5, 1) */
+        double M = 0.0;
+        for (int b = 0; b < q; ++b)
+            if (fabs((double)y[b]) > M) M = fabs((double)y[b]);
+        int s = 0;
+        if (M > 0.0) {
+            int e;
+            frexp(M, &e);
+            s = 53 - (e - 1);
+        }
+        uint64_t w[ORC_MAXQ];
+        for (int b = 0; b < q; ++b)
+            w[b] = (uint64_t)floor(ldexp(fabs((double)y[b]), s));
         uint32_t cnt = 0;
         for (uint32_t i = 0; i < k_in; ++i) {
             uint32_t id = ids[qi * k_in + i];
             if (id == ORC_PAD_ID) continue;
             if ((uint64_t)id >= n) { free(list); return -2; }
             const uint64_t *h = codes + (uint64_t)id * W;
-            double a = 0.0;
+            uint64_t a = 0;
             for (int b = 0; b < q; ++b) {
                 int query_bit = y[b] > 0.0f;
-                if (code_bit(h, b) != query_bit) a += __builtin_fabs((double)y[b]);
+                if (code_bit(h, b) != query_bit) a += w[b];
             }
             list[cnt].a = a;
             list[cnt].id = id;
@@ -533,7 +551,7 @@ int orc_rerank_asym(const uint64_t *codes, uint64_t n, int q, const float *proj,
         qsort(list, cnt, sizeof(orc_scored), scored_cmp);
         for (uint32_t p = 0; p < k; ++p) {
             out_ids[qi * k + p] = p < cnt ? list[p].id : ORC_PAD_ID;
-            out_a[qi * k + p] = p < cnt ? list[p].a : -1.0;
+            out_a[qi * k + p] = p < cnt ? ldexp((double)list[p].a, -s) : -1.0;
         }
     }
     free(list);

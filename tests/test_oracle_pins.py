@@ -444,8 +444,8 @@ def _expected_rerank(codes, y, ids, k, weights):
 
 @pytest.mark.parametrize("q", [64, 128, 256])
 def test_rerank_asym_integer_weights(orc, q):
-    """|y_b| = b + 1 with random signs: every partial sum is an exact integer,
-    so the distance equals the integer dot product of the disagreement bits
+    """|y_b| = b + 1 with random signs: the weights lie on the grid, so the
+    distance equals the integer dot product of the disagreement bits
     with (1, ..., q) -- a wrong bit index, sign test or dropped term changes
     it -- and the order is numpy's lexsort of (distance, id).  Row 0 has
     padding inside it and fewer valid candidates than k."""
@@ -510,6 +510,45 @@ def test_rerank_asym_sign_flip_invariance(orc):
     a_ids, a_a = orc.rerank_asym(codes, y, ids, 50)
     b_ids, b_a = orc.rerank_asym(codes ^ mask[None, :], y2, ids, 50)
     assert np.array_equal(a_ids, b_ids) and np.array_equal(a_a, b_a)
+
+
+def _permute_bits(codes, perm):
+    """Code bit perm[b] moves to bit b, for every code."""
+    bits = np.ascontiguousarray(unpack(codes)[:, perm])
+    return np.ascontiguousarray(np.packbits(bits, axis=1, bitorder="little")).view(np.uint64)
+
+
+def test_rerank_asym_sum_is_order_free(orc):
+    """The sum is exact, so it does not depend on the order of the bits:
+    permuting the bits of every code and the query's values the same way
+    gives the same ids and distances, bit for bit (a sum rounded term by
+    term would differ in the last bits)."""
+    q = 256
+    codes, _ = synth.lsh_projections(1500, q, 33)
+    _, y = synth.lsh_projections(4, q, 34)
+    rng = np.random.default_rng(8)
+    ids = np.stack([rng.choice(1500, size=400, replace=False) for _ in range(4)]).astype(np.uint32)
+    perm = rng.permutation(q)
+    a_ids, a_a = orc.rerank_asym(codes, y, ids, 400)
+    b_ids, b_a = orc.rerank_asym(_permute_bits(codes, perm), np.ascontiguousarray(y[:, perm]), ids, 400)
+    assert np.array_equal(a_ids, b_ids) and np.array_equal(a_a, b_a)
+
+
+def test_rerank_asym_grid(orc):
+    """The fixed-point grid: with the largest |y_b| = 1.5 (binary exponent 0)
+    the weights are floor(|y_b| 2^53); a weight of 2^-60 rounds to 0 and
+    adds nothing, one of 3 * 2^-52 is kept exactly."""
+    codes = np.array([[0], [1 << 1], [1 << 2], [(1 << 1) | (1 << 2)]], dtype=np.uint64)
+    y = np.zeros((1, 64), dtype=np.float32)
+    y[0, 0] = 1.5            # query bit 0 set; every code disagrees there
+    y[0, 1] = 2.0 ** -60     # below the grid
+    y[0, 2] = 3 * 2.0 ** -52
+    ids, a = orc.rerank_asym(codes, y, np.arange(4, dtype=np.uint32)[None, :], 4)
+    # the query's bits 0..2 are set: codes 2 and 3 (bit 2 set) disagree on
+    # bit 0 and at most on bit 1, whose weight is 0: 1.5 exactly; codes 0
+    # and 1 also disagree on bit 2: 1.5 + 3 * 2^-52 (weight 6 on the grid)
+    assert ids[0].tolist() == [2, 3, 0, 1]
+    assert a[0].tolist() == [1.5, 1.5, 1.5 + 3 * 2.0 ** -52, 1.5 + 3 * 2.0 ** -52]
 
 
 def test_rerank_asym_edges(orc):
