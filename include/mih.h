@@ -302,8 +302,11 @@ MIH_API mih_status mih_merge_topk(const uint32_t *ids, const int32_t *dist, uint
  * query row i with real projections y = proj[i] (its code is their signs:
  * bit b set where y_b > 0) and database code h,
  *     a(y, h) = sum of |y_b| over the bits b where h_b != [y_b > 0],
- * accumulated in fp64 in increasing b (so the value is one fixed IEEE
- * number).  Row i's candidates are ordered by (a, id) and the first k kept.
+ * summed exactly on a fixed-point grid: with 2^E <= max_b |y_b| < 2^(E+1),
+ * w_b = floor(|y_b| 2^(53-E)), the integer sum of the w_b over the
+ * disagreeing bits (below 2^62) is exact, and a = that sum rounded to double
+ * times 2^-(53-E).  Row i's candidates are ordered by (integer sum, id) and
+ * the first k kept.
  * Leaves the exact-Hamming contract of mih_knn: with every |y_b| equal it
  * orders by Hamming distance, otherwise by the weighted form.
  *

@@ -5,13 +5,16 @@
 // hashing supplies the candidates and the asymmetric distance culls them.
 // The distance (the paper gives no formula) is
 //     a(y, h) = sum of |y_b| over the bits b where h_b != [y_b > 0],
-// with y the query's q real projections (their signs are its code).  It is
-// accumulated in fp64, bit 0 first, so the result is one fixed IEEE value.
+// with y the query's q real projections (their signs are its code), summed
+// exactly on a fixed-point grid: with 2^E <= max |y_b| < 2^(E+1) the weights
+// are w_b = floor(|y_b| 2^(53-E)) (below 2^54), their sum is an exact
+// integer (below 2^62) in any order, and a is that sum rounded to double,
+// times 2^-(53-E).
 //
-// One CTA per query row: the row's |y_b| and sign code go to shared memory,
+// One CTA per query row: the row's weights and sign code go to shared memory,
 // every thread scores candidates (a 16- or 32-byte code gathered by id, then
-// one fp64 add per disagreeing bit, visited in increasing bit order), and a
-// bitonic network over the row sorts the (a, id) pairs in shared memory.
+// one 64-bit integer add per disagreeing bit), and a bitonic network over the
+// row sorts the (sum, id) pairs in shared memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,34 +36,53 @@ struct RerankArgs {
     unsigned int* bad;    // set when a candidate id is >= n
 };
 
-// Shared memory of a row: sort keys (the bit patterns of the nonnegative
-// fp64 sums, which order like the sums), the sign code, ids, |y_b|.
+// Shared memory of a row: sort keys (the integer sums), the weights, the
+// sign code, ids, and the row's largest |y_b| (as its fp32 bit pattern).
 template <int W>
 constexpr size_t rerank_smem_bytes(uint32_t P) {
-    return static_cast<size_t>(P) * 12 + W * 8 + W * 64 * 4;
+    return static_cast<size_t>(P) * 12 + W * 64 * 8 + W * 8 + 8;
+}
+
+// 2^e as a double, for -1022 <= e <= 1023 (built from its bits: exact).
+__device__ __forceinline__ double pow2(int e) {
+    return __longlong_as_double(static_cast<long long>(1023 + e) << 52);
 }
 
 template <int W>
 __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t* key = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* qcode = key + a.P;
+    uint64_t* wt = key + a.P;          // [64 W] grid weights
+    uint64_t* qcode = wt + 64 * W;     // [W] sign code
     uint32_t* cid = reinterpret_cast<uint32_t*>(qcode + W);
-    float* wy = reinterpret_cast<float*>(cid + a.P);
+    uint32_t* ymax = cid + a.P;        // largest |y_b|, fp32 bits (nonnegative: they order as integers)
 
     const uint64_t row = blockIdx.x;
     const float* y = a.proj + row * (64 * W);
-    for (int b = threadIdx.x; b < 64 * W; b += blockDim.x) wy[b] = fabsf(__ldg(y + b));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
+    if (threadIdx.x == 0) *ymax = 0u;
+    __syncthreads();
     for (int w32 = warp; w32 < 2 * W; w32 += warps) {
-        const unsigned bits = __ballot_sync(0xffffffffu, __ldg(y + w32 * 32 + lane) > 0.f);
-        if (lane == 0) reinterpret_cast<uint32_t*>(qcode)[w32] = bits;   // little-endian words
+        const float v = __ldg(y + w32 * 32 + lane);
+        const unsigned bits = __ballot_sync(0xffffffffu, v > 0.f);
+        const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(v)));
+        if (lane == 0) {
+            reinterpret_cast<uint32_t*>(qcode)[w32] = bits;   // little-endian words
+            atomicMax(ymax, m);
+        }
     }
     __syncthreads();
+    // the grid: s = 53 - E, E the binary exponent of the largest |y_b|
+    const double M = static_cast<double>(__uint_as_float(*ymax));
+    const int s = M > 0.0 ? 53 - (static_cast<int>((__double_as_longlong(M) >> 52) & 0x7FF) - 1023) : 0;
+    const double scale = pow2(s);
+    for (int b = threadIdx.x; b < 64 * W; b += blockDim.x)
+        wt[b] = __double2ull_rz(static_cast<double>(fabsf(__ldg(y + b))) * scale);   // exact product, floor
+    __syncthreads();
 
-    Code<W> g;
+    uint32_t g[2 * W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) g.w[w] = qcode[w];
+    for (int w = 0; w < 2 * W; ++w) g[w] = reinterpret_cast<const uint32_t*>(qcode)[w];
     for (uint32_t i = threadIdx.x; i < a.P; i += blockDim.x) {
         uint64_t kk = ~0ull;
         uint32_t id = kPadId;
@@ -72,24 +94,24 @@ __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
             }
             if (id != kPadId) {
                 const Code<W> h = load_code<W>(a.codes, id);
-                double s = 0.0;
+                uint64_t acc = 0;
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    uint64_t x = h.w[w] ^ g.w[w];
+                for (int w = 0; w < 2 * W; ++w) {
+                    const uint64_t hw = h.w[w >> 1];
+                    uint32_t x = static_cast<uint32_t>((w & 1) ? (hw >> 32) : hw) ^ g[w];
                     while (x) {
-                        const int b = __ffsll(static_cast<long long>(x)) - 1;
-                        s = __dadd_rn(s, static_cast<double>(wy[64 * w + b]));
+                        acc += wt[32 * w + __ffs(x) - 1];
                         x &= x - 1;
                     }
                 }
-                kk = static_cast<uint64_t>(__double_as_longlong(s));
+                kk = acc;
             }
         }
         key[i] = kk;
         cid[i] = id;
     }
 
-    // bitonic sort of (key, id), ascending; padding (key ~0, id ~0) goes last
+    // bitonic sort of (sum, id), ascending; padding (key ~0, id ~0) goes last
     for (uint32_t size = 2; size <= a.P; size <<= 1) {
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
             __syncthreads();
@@ -112,7 +134,7 @@ __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
     for (uint32_t p = threadIdx.x; p < a.k; p += blockDim.x) {
         const bool real = p < a.P && key[p] != ~0ull;
         a.out_ids[row * a.k + p] = real ? cid[p] : kPadId;
-        a.out_a[row * a.k + p] = real ? __longlong_as_double(static_cast<long long>(key[p])) : -1.0;
+        a.out_a[row * a.k + p] = real ? __ull2double_rn(key[p]) * pow2(-s) : -1.0;
     }
 }
 

@@ -1,7 +1,7 @@
 """Re-ranking by the asymmetric Hamming distance (Sec. 5.1 re-ranking phase,
 Conclusion): the CUDA kernel against the oracle, bit for bit on ids and on
-the fp64 distances (both sides add the same fp32 magnitudes in the same
-order), on ragged rows, every code length, sort widths from 2 to 8192, k
+the distances (both sides sum the same fixed-point weights exactly and round
+once), on ragged rows, every code length, sort widths from 2 to 8192, k
 below and above the row length, and after a real mih_knn.
 """
 import numpy as np
@@ -61,6 +61,31 @@ def test_rerank_ties_and_zero_weights(gpu_lib, orc):
     want = orc.rerank_asym(codes, proj, ids, 500)
     got = _run(gpu_lib, codes, proj, ids, q, 500)
     assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
+def test_rerank_grid_extremes(gpu_lib, orc):
+    """The per-row grid at the ends of the fp32 range: an all-zero row, rows
+    scaled by 1e30 and 1e-30, one with subnormal values beside normal ones,
+    one with a single nonzero value, one with values far below its largest."""
+    q, n = 128, 4000
+    codes, _ = synth.lsh_projections(n, q, 70)
+    _, base = synth.lsh_projections(6, q, 71)
+    proj = base.astype(np.float64)
+    proj[0] = 0.0
+    proj[1] *= 1e30
+    proj[2] *= 1e-30
+    proj[3, ::2] *= 1e-40        # subnormal in fp32
+    proj[4] = 0.0
+    proj[4, 77] = -3.25
+    proj[5, 1::2] *= 2.0 ** -70   # below the grid of the row's largest value
+    proj = proj.astype(np.float32)
+    rng = np.random.default_rng(72)
+    ids = np.stack([rng.choice(n, size=500, replace=False) for _ in range(6)]).astype(np.uint32)
+    want_ids, want_a = orc.rerank_asym(codes, proj, ids, 200)
+    got_ids, got_a = _run(gpu_lib, codes, proj, ids, q, 200)
+    assert np.array_equal(got_ids, want_ids)
+    assert np.array_equal(got_a, want_a)
+    assert (got_a[0] == 0.0).all()
 
 
 def test_rerank_after_mih_knn(gpu_lib, orc):
