@@ -1134,36 +1134,16 @@ __global__ void __launch_bounds__(Shape::kWarps * 32, Shape::kMinBlocks) search_
                     near |= (valid[k] && d <= far) ? (1u << k) : 0u;
                 }
                 if (!__any_sync(0xFFFFFFFFu, near != 0u)) continue;
-                if (__reduce_max_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(near))) >= 3u) {
-                    // many near records (no bound yet, or exact counters):
-                    // all four of every lane at once
-                    uint32_t pos[4];
-                    uint32_t rec[4][R];
+                uint32_t pos[4];
+                uint32_t rec[4][R];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        pos[k] = cur.pos + (4u * g + k - r_lo);
+                for (int k = 0; k < 4; ++k) {
+                    pos[k] = cur.pos + (4u * g + k - r_lo);
 #pragma unroll
-                        for (int i = 0; i < R; ++i) rec[k][i] = wv[k * R + i];
-                    }
-                    process_records<R, MODE, 4>(a, whist, cur.q, j, rho, cur.bnd, count_new, gq, th, ids, pos,
-                                                valid, rec, unique);
-                    continue;
+                    for (int i = 0; i < R; ++i) rec[k][i] = wv[k * R + i];
                 }
-                // the usual case: a lane holds one near record or two; each
-                // lane takes its next one per round (the others idle)
-                do {
-                    const bool has = near != 0u;
-                    const uint32_t k = has ? static_cast<uint32_t>(__ffs(near) - 1) : 0u;
-                    near &= near - 1u;
-                    uint32_t rec1[1][R];
-#pragma unroll
-                    for (int i = 0; i < R; ++i)
-                        rec1[0][i] = k == 0u ? wv[i] : (k == 1u ? wv[R + i] : (k == 2u ? wv[2 * R + i] : wv[3 * R + i]));
-                    const uint32_t pos1[1] = {cur.pos + (4u * g + k - r_lo)};
-                    const bool valid1[1] = {has};
-                    process_records<R, MODE, 1>(a, whist, cur.q, j, rho, cur.bnd, count_new, gq, th, ids, pos1,
-                                                valid1, rec1, unique);
-                } while (__any_sync(0xFFFFFFFFu, near != 0u));
+                process_records<R, MODE, 4>(a, whist, cur.q, j, rho, cur.bnd, count_new, gq, th, ids, pos, valid,
+                                            rec, unique);
             }
         } else {
         const CandSource src{nullptr, a.tables[j].ids, false};
