@@ -11,10 +11,12 @@
 // integer (below 2^62) in any order, and a is that sum rounded to double,
 // times 2^-(53-E).
 //
-// One CTA per query row: the row's weights and sign code go to shared memory,
-// every thread scores candidates (a 16- or 32-byte code gathered by id, then
-// one 64-bit integer add per disagreeing bit), and a bitonic network over the
-// row sorts the (sum, id) pairs in shared memory.
+// Rows of up to 256 candidates take one warp each (the row sorted in
+// registers and by shuffles); longer rows one CTA each: the row's weights and
+// sign code go to shared memory, every thread scores candidates (a 16- or
+// 32-byte code gathered by id, then one 64-bit integer add per disagreeing
+// bit), and a bitonic network over the row sorts the (sum, id) pairs in
+// shared memory.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -138,8 +140,155 @@ __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
     }
 }
 
+// Rows of up to 256 candidates: one warp per row, no block barriers.  The
+// row's P = 32 E slots are held E per lane (slot x = 32 e + lane): the lane
+// scores its E candidates with their gathers in flight together, then a
+// bitonic network sorts the slots, exchanging across lanes by shuffles
+// (strides below 32) and within a lane in registers (strides 32 and up).
+constexpr int kRowWarps = 8;
+
+// Keep the smaller (ascending) or larger of (k, i) and its partner (pk, pi).
+__device__ __forceinline__ void keep_side(uint64_t& k, uint32_t& i, uint64_t pk, uint32_t pi, bool smaller) {
+    const bool mine_less = k < pk || (k == pk && i < pi);
+    if (mine_less != smaller) {
+        k = pk;
+        i = pi;
+    }
+}
+
+template <int W, int E>
+__global__ void __launch_bounds__(kRowWarps * 32) rerank_warp_kernel(RerankArgs a, uint32_t nq) {
+    __shared__ uint64_t s_wt[kRowWarps][64 * W];
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t row = static_cast<uint64_t>(blockIdx.x) * kRowWarps + warp;
+    if (row >= nq) return;   // warp-uniform; the kernel has no block barrier
+    uint64_t* wt = s_wt[warp];
+    const float* y = a.proj + row * (64 * W);
+
+    // sign code (ballots) and the grid of the largest |y_b|
+    uint32_t g[2 * W];
+    float v[2 * W];
+    uint32_t mx = 0u;
+#pragma unroll
+    for (int w = 0; w < 2 * W; ++w) {
+        v[w] = __ldg(y + 32 * w + lane);
+        g[w] = __ballot_sync(0xffffffffu, v[w] > 0.f);
+        mx = max(mx, __float_as_uint(fabsf(v[w])));
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    const double M = static_cast<double>(__uint_as_float(mx));
+    const int s = M > 0.0 ? 53 - (static_cast<int>((__double_as_longlong(M) >> 52) & 0x7FF) - 1023) : 0;
+    const double scale = pow2(s);
+#pragma unroll
+    for (int w = 0; w < 2 * W; ++w)
+        wt[32 * w + lane] = __double2ull_rz(static_cast<double>(fabsf(v[w])) * scale);   // exact product, floor
+    __syncwarp();
+
+    uint64_t key[E];
+    uint32_t cid[E];
+    Code<W> h[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t x = 32u * e + lane;
+        cid[e] = x < a.k_in ? __ldg(a.ids + row * a.k_in + x) : kPadId;
+        if (cid[e] != kPadId && cid[e] >= a.n) {
+            atomicOr(a.bad, 1u);
+            cid[e] = kPadId;
+        }
+        if (cid[e] != kPadId) h[e] = load_code<W>(a.codes, cid[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        key[e] = ~0ull;
+        if (cid[e] != kPadId) {
+            uint64_t acc = 0;
+#pragma unroll
+            for (int w = 0; w < 2 * W; ++w) {
+                const uint64_t hw = h[e].w[w >> 1];
+                uint32_t x = static_cast<uint32_t>((w & 1) ? (hw >> 32) : hw) ^ g[w];
+                while (x) {
+                    acc += wt[32 * w + __ffs(x) - 1];
+                    x &= x - 1;
+                }
+            }
+            key[e] = acc;
+        }
+    }
+
+    // bitonic sort of the 32 E slots by (sum, id), ascending
+#pragma unroll
+    for (uint32_t size = 2; size <= 32u * E; size <<= 1) {
+#pragma unroll
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int se = static_cast<int>(stride >> 5);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int f = e ^ se;
+                    if (f > e) {
+                        const bool asc = ((32u * e + lane) & size) == 0;
+                        const bool greater = key[e] > key[f] || (key[e] == key[f] && cid[e] > cid[f]);
+                        if (greater == asc) {
+                            const uint64_t tk = key[e];
+                            const uint32_t ti = cid[e];
+                            key[e] = key[f];
+                            cid[e] = cid[f];
+                            key[f] = tk;
+                            cid[f] = ti;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint64_t pk = __shfl_xor_sync(0xffffffffu, key[e], stride);
+                    const uint32_t pi = __shfl_xor_sync(0xffffffffu, cid[e], stride);
+                    const bool asc = ((32u * e + lane) & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    keep_side(key[e], cid[e], pk, pi, lower == asc);
+                }
+            }
+        }
+    }
+
+    const double unscale = pow2(-s);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const uint32_t x = 32u * e + lane;
+        if (x < a.k) {
+            const bool real = key[e] != ~0ull;
+            a.out_ids[row * a.k + x] = real ? cid[e] : kPadId;
+            a.out_a[row * a.k + x] = real ? __ull2double_rn(key[e]) * unscale : -1.0;
+        }
+    }
+    for (uint32_t x = 32u * E + lane; x < a.k; x += 32) {
+        a.out_ids[row * a.k + x] = kPadId;
+        a.out_a[row * a.k + x] = -1.0;
+    }
+}
+
+template <int W, int E>
+mih_status launch_rerank_rows(const RerankArgs& a, uint32_t nq, cudaStream_t s) {
+    const unsigned blocks = (nq + kRowWarps - 1) / kRowWarps;
+    main_kernel_begin(s);
+    {
+        KernelSpan span(s, MIH_PROF_RERANK);
+        rerank_warp_kernel<W, E><<<blocks, kRowWarps * 32, 0, s>>>(a, nq);
+    }
+    main_kernel_end(s);
+    MIH_LAUNCH_CHECK();
+    return MIH_OK;
+}
+
 template <int W>
 mih_status launch_rerank(const RerankArgs& a, uint32_t nq, cudaStream_t s) {
+    // rows of up to 256 candidates: a warp per row
+    if (a.P <= 32) return launch_rerank_rows<W, 1>(a, nq, s);
+    if (a.P == 64) return launch_rerank_rows<W, 2>(a, nq, s);
+    if (a.P == 128) return launch_rerank_rows<W, 4>(a, nq, s);
+    if (a.P == 256) return launch_rerank_rows<W, 8>(a, nq, s);
+
     const size_t smem = rerank_smem_bytes<W>(a.P);
     if (smem > 48 * 1024)
         MIH_CUDA(cudaFuncSetAttribute(rerank_asym_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,

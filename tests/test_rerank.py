@@ -1,8 +1,9 @@
 """Re-ranking by the asymmetric Hamming distance (Sec. 5.1 re-ranking phase,
 Conclusion): the CUDA kernel against the oracle, bit for bit on ids and on
 the distances (both sides sum the same fixed-point weights exactly and round
-once), on ragged rows, every code length, sort widths from 2 to 8192, k
-below and above the row length, and after a real mih_knn.
+once), on ragged rows, every code length, rows sorted by one warp (up to 256
+candidates) and by a CTA (up to 8192), k below and above the row length, and
+after a real mih_knn.
 """
 import numpy as np
 import pytest
@@ -31,6 +32,10 @@ def _run(mih, codes_np, proj_np, ids_np, q, k):
     (128, 5000, 9, 1000, 1005),
     (256, 5000, 23, 300, 64),
     (128, 20000, 3, 8192, 8192),
+    (64, 3000, 11, 32, 40),      # one slot per lane, k past the row
+    (128, 5000, 29, 33, 7),      # 64 slots
+    (256, 5000, 19, 256, 300),   # 256 slots (the widest warp-per-row case), k past the row
+    (128, 5000, 5, 257, 20),     # the first width sorted by a CTA
 ])
 def test_rerank_matches_oracle(gpu_lib, orc, q, n, nq, k_in, k):
     codes, _ = synth.lsh_projections(n, q, 40 + q)
