@@ -863,10 +863,24 @@ struct StreamShape {
     static constexpr int kStages = NS;
     static constexpr uint32_t kSlot = SB + 16;   // + one 8-byte code of realignment (W = 1)
     static constexpr size_t kSmem = static_cast<size_t>(NW) * NS * kSlot;
-    // resident CTAs per SM the stage ring leaves room for (sets the register budget)
-    static constexpr int kMinBlocks = (227 * 1024) / (kSmem + 8 * 1024) > 0 ? (227 * 1024) / (kSmem + 8 * 1024) : 1;
     static_assert(NS >= 2 && NS <= 4, "stage ring of 2 to 4 slots");
 };
+
+// Static shared memory of the slice kernel for W-word codes: a histogram of
+// distances 0..64 W per warp, the barriers, and (whole codes only: records
+// never read them) the substring layout of up to 64 W tables.
+template <class Shape, int W, bool REDUCED>
+constexpr size_t stream_static_smem() {
+    return static_cast<size_t>(Shape::kWarps) * (64 * W + 1) * 4 + static_cast<size_t>(Shape::kWarps) * Shape::kStages * 8 +
+           16 + (REDUCED ? 8 : static_cast<size_t>(64 * W) * 4 * (1 + 2 * W));
+}
+// Resident CTAs per SM that shared memory allows (228 KB per SM, 1 KB of it
+// reserved per CTA); sets the kernel's register budget.
+template <class Shape, int W, bool REDUCED>
+constexpr int stream_min_blocks() {
+    constexpr size_t per = Shape::kSmem + stream_static_smem<Shape, W, REDUCED>() + 1024;
+    return (228 * 1024) / per > 0 ? static_cast<int>((228 * 1024) / per) : 1;
+}
 #ifndef MIH_STREAM_STAGES
 #define MIH_STREAM_STAGES 2
 #endif
@@ -985,7 +999,8 @@ __device__ __forceinline__ uint32_t issue_stage(const SearchArgs& a, const Stage
 }
 
 template <int W, int MODE, bool ALIGNED, class Shape>
-__global__ void __launch_bounds__(Shape::kWarps * 32, Shape::kMinBlocks) search_stream_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(Shape::kWarps * 32, (stream_min_blocks<Shape, W, ALIGNED>()))
+    search_stream_kernel(SearchArgs a) {
     constexpr int kStreamWarps = Shape::kWarps;
     constexpr int kStages = Shape::kStages;
     constexpr uint32_t kStageSlot = Shape::kSlot;
@@ -993,14 +1008,18 @@ __global__ void __launch_bounds__(Shape::kWarps * 32, Shape::kMinBlocks) search_
     // aligned tables (every substring one 32-bit word) keep inline records
     // without their own word; the others keep whole codes
     constexpr bool REDUCED = ALIGNED;
+    // distances 0..64 W; up to 64 W tables (m <= q), whose layout only
+    // whole codes read
+    constexpr int kBins = 64 * W + 1;
+    constexpr int kTabs = REDUCED ? 1 : 64 * W;
     extern __shared__ __align__(128) unsigned char dsm[];
-    __shared__ int s_len[kMaxTables];
-    __shared__ uint32_t s_mask[kMaxTables * 2 * W];
-    __shared__ uint32_t s_hist[kStreamWarps][kHistBins];
+    __shared__ int s_len[kTabs];
+    __shared__ uint32_t s_mask[kTabs * 2 * W];
+    __shared__ uint32_t s_hist[kStreamWarps][kBins];
     __shared__ __align__(8) uint64_t s_bar[kStreamWarps][kStages];
     __shared__ __align__(8) uint64_t s_never;   // a barrier no copy completes (timeout test)
-    build_layout(a.tables, a.m, W, s_len, s_mask);
-    for (int i = threadIdx.x; i < kStreamWarps * kHistBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+    if constexpr (!REDUCED) build_layout(a.tables, a.m, W, s_len, s_mask);
+    for (int i = threadIdx.x; i < kStreamWarps * kBins; i += blockDim.x) (&s_hist[0][0])[i] = 0;
     const int warp = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     if (lane == 0) {
