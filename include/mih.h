@@ -123,16 +123,16 @@ typedef struct {
                               mih_cost_layout proposes lengths. */
     int32_t slice_shape;   /* Shape of the kernel that streams big buckets in the
                               k-NN waves (a launch choice; results unchanged):
-                              MIH_SLICE_SHAPE_4K_8W (default) 4 KB stages, 8 warps
-                              per CTA, 2 stages in flight per warp;
+                              MIH_SLICE_SHAPE_3K_8W (default) 3 KB stages, 8 warps
+                              per CTA, 2 stages in flight per warp (4 CTAs per SM);
                               MIH_SLICE_SHAPE_8K_4W 8 KB stages, 4 warps;
-                              MIH_SLICE_SHAPE_4K_8W_3S 4 KB stages, 8 warps, 3 in
-                              flight.  mih_tune_search picks one by timing. */
+                              MIH_SLICE_SHAPE_4K_8W 4 KB stages, 8 warps (3 CTAs
+                              per SM).  mih_tune_search picks one by timing. */
     int32_t reserved[5];   /* must be zero */
 } mih_params;
 
 /* mih_params.slice_shape values. */
-enum { MIH_SLICE_SHAPE_4K_8W = 0, MIH_SLICE_SHAPE_8K_4W = 1, MIH_SLICE_SHAPE_4K_8W_3S = 2 };
+enum { MIH_SLICE_SHAPE_3K_8W = 0, MIH_SLICE_SHAPE_8K_4W = 1, MIH_SLICE_SHAPE_4K_8W = 2 };
 
 /* mih_params.executor (not part of the paper: a launch strategy). */
 enum {

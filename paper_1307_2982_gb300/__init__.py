@@ -26,8 +26,8 @@ MIH_OK, MIH_EINVAL, MIH_ENOMEM, MIH_ECUDA, MIH_EOVERFLOW, MIH_ETIMEOUT, MIH_EINT
 MIH_TABLE_AUTO, MIH_TABLE_DIRECT, MIH_TABLE_SPARSE = 0, 1, 2
 MIH_EXEC_AUTO, MIH_EXEC_HOST, MIH_EXEC_GRAPH = 0, 1, 2
 MIH_SCAN_AUTO, MIH_SCAN_POPC, MIH_SCAN_TENSOR = 0, 1, 2
-MIH_SLICE_SHAPE_4K_8W, MIH_SLICE_SHAPE_8K_4W, MIH_SLICE_SHAPE_4K_8W_3S = 0, 1, 2
-SLICE_SHAPES = ("4KB stages x 8 warps x 2", "8KB stages x 4 warps x 2", "4KB stages x 8 warps x 3")
+MIH_SLICE_SHAPE_3K_8W, MIH_SLICE_SHAPE_8K_4W, MIH_SLICE_SHAPE_4K_8W = 0, 1, 2
+SLICE_SHAPES = ("3KB stages x 8 warps x 2", "8KB stages x 4 warps x 2", "4KB stages x 8 warps x 2")
 MIH_MAX_K = 8192
 PAD_ID = 0xFFFFFFFF
 

@@ -355,7 +355,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     }
     int kind_req = MIH_TABLE_AUTO;
     if (params) {
-        if (params->slice_shape < MIH_SLICE_SHAPE_4K_8W || params->slice_shape > MIH_SLICE_SHAPE_4K_8W_3S) {
+        if (params->slice_shape < MIH_SLICE_SHAPE_3K_8W || params->slice_shape > MIH_SLICE_SHAPE_4K_8W) {
             set_error("mih_build: unknown slice_shape %d", params->slice_shape);
             return MIH_EINVAL;
         }
@@ -398,7 +398,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->probe = (!params || params->probe == 0) ? 1024 : (params->probe < 0 ? 0 : params->probe);
     ix->executor = params ? params->executor : MIH_EXEC_AUTO;
     ix->tail_from = (!params || params->tail_from <= 0) ? -1 : params->tail_from;
-    ix->slice_shape = params ? params->slice_shape : MIH_SLICE_SHAPE_4K_8W;
+    ix->slice_shape = params ? params->slice_shape : MIH_SLICE_SHAPE_3K_8W;
     if (params && params->bit_order) {
         // Optimised substrings (Sec. 5.5): the tables see codes whose bits are
         // permuted; the index keeps that copy and the order for the queries.

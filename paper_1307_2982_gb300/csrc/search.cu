@@ -41,7 +41,7 @@ namespace {
 constexpr int kSearchThreads = 256;
 constexpr uint32_t kSliceEntries = 1024;   // big-bucket slice of whole codes
 #ifndef MIH_STAGE_BYTES
-#define MIH_STAGE_BYTES 4096
+#define MIH_STAGE_BYTES 3072
 #endif
 constexpr uint32_t kDefaultStageBytes = MIH_STAGE_BYTES;   // one shared-memory stage of the slice kernel
 
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(kSearchThreads, MIH_BIG_MIN_BLOCKS) search_big
 // ------------------------------------------------------- streamed slices
 // With inline codes every big-bucket slice is one contiguous run of codes.
 // Each warp streams its slices through a ring of kStages shared-memory stages
-// (4 KB in the default shape): lane 0 keeps bulk asynchronous copies
+// (3 KB in the default shape): lane 0 keeps bulk asynchronous copies
 // (cp.async.bulk, completion counted on an mbarrier per stage) of the next
 // kStages - 1 stages in flight
 // while the warp verifies the current one.  Every wait on an mbarrier is
@@ -887,9 +887,10 @@ constexpr int stream_min_blocks() {
 #ifndef MIH_STREAM_WARPS
 #define MIH_STREAM_WARPS 8
 #endif
-using Shape0 = StreamShape<kDefaultStageBytes, MIH_STREAM_WARPS, MIH_STREAM_STAGES>;   // the default
-using Shape1 = StreamShape<2 * kDefaultStageBytes, 4, 2>;                             // larger stages, fewer warps
-using Shape2 = StreamShape<kDefaultStageBytes, 8, 3>;                                  // a deeper ring
+// The default: 3 KB stages leave room for 4 CTAs (32 warps) per SM.
+using Shape0 = StreamShape<kDefaultStageBytes, MIH_STREAM_WARPS, MIH_STREAM_STAGES>;
+using Shape1 = StreamShape<8192, 4, 2>;   // larger stages, fewer warps
+using Shape2 = StreamShape<4096, 8, 2>;   // 4 KB stages, 3 CTAs per SM
 constexpr int kStreamVariants = 3;
 
 // Largest bulk copy issue_stage makes for one stage: records start up to three
@@ -1067,7 +1068,7 @@ __global__ void __launch_bounds__(Shape::kWarps * 32, (stream_min_blocks<Shape, 
         if (n3.valid) n3.shift = issue_stage<W, REDUCED>(a, n3, slot0 + 3 * kStageSlot, bar0 + 3);
     }
     // entries per lane and batch: whole codes, B of them per lane at a time
-    // (a 4 KB stage is 1, 2 or 4 batches for W = 4, 2, 1), or records
+    // (up to 32 * 4 codes per batch), or records
     constexpr int kPer = static_cast<int>(stage_entries<W, REDUCED, SB>());
     constexpr int B = kPer / 32 < 4 ? kPer / 32 : 4;
     constexpr int R = 2 * W - 1;
