@@ -56,11 +56,14 @@ __host__ __device__ constexpr uint32_t stage_entries() {
     return REDUCED ? 4u * (SB / (16u * (2 * W - 1))) - 3u : SB / (8 * W);
 }
 
-// Entries per big-bucket slice: 1024 whole codes, or four full stages of
-// records, so that no slice ends in a nearly empty stage.
+// Entries per big-bucket slice: 1024 whole codes, or MIH_SLICE_STAGES (4)
+// full stages of records, so that no slice ends in a nearly empty stage.
+#ifndef MIH_SLICE_STAGES
+#define MIH_SLICE_STAGES 4
+#endif
 template <int W, bool ALIGNED, uint32_t SB = kDefaultStageBytes>
 __host__ __device__ constexpr uint32_t slice_entries() {
-    return ALIGNED ? 4u * stage_entries<W, true, SB>() : kSliceEntries;
+    return ALIGNED ? static_cast<uint32_t>(MIH_SLICE_STAGES) * stage_entries<W, true, SB>() : kSliceEntries;
 }
 constexpr uint32_t kScanChunk = 4096;      // codes per chunk of a full verification pass
 constexpr int kQueryShift = 41;            // composite entry: q << 41 | d << 32 | id
