@@ -56,10 +56,13 @@ __host__ __device__ constexpr uint32_t stage_entries() {
     return REDUCED ? 4u * (SB / (16u * (2 * W - 1))) - 3u : SB / (8 * W);
 }
 
-// Entries per big-bucket slice: 1024 whole codes, or MIH_SLICE_STAGES (4)
+// Entries per big-bucket slice: 1024 whole codes, or MIH_SLICE_STAGES (6)
 // full stages of records, so that no slice ends in a nearly empty stage.
+// (3, 4, 6 and 8 stages of 3 KB: 6.21, 6.11, 6.08 and 6.14 ms per 1e9 x
+// 128-bit batch: longer slices mean fewer descriptors for the chunk kernel
+// to write, shorter ones a better balanced end of each wave.)
 #ifndef MIH_SLICE_STAGES
-#define MIH_SLICE_STAGES 4
+#define MIH_SLICE_STAGES 6
 #endif
 template <int W, bool ALIGNED, uint32_t SB = kDefaultStageBytes>
 __host__ __device__ constexpr uint32_t slice_entries() {
