@@ -1725,6 +1725,8 @@ __global__ void init_knn_kernel(uint32_t nq, uint64_t n, int32_t* t_lo, int32_t*
 // least min(k, n) probed codes within D is a valid bound; queries that probe
 // fewer codes keep bound = -1 (histogram-only steps until one exists).
 
+constexpr int kProbeBatch = 8;   // records per lane in flight in the bound probe
+
 template <int W>
 __global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __restrict__ tables, int m, int qbits,
                                                           const uint64_t* __restrict__ codes,
@@ -1741,12 +1743,18 @@ __global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __res
     const uint32_t q = blockIdx.x * 8 + warp;
     if (q >= nq) return;
     const Code<W> g = load_query<W>(queries, q);
+    // the query's own bucket in every table: lane l looks up tables
+    // j0 + l, all 32 lookups in flight together
+    uint32_t lb = 0, le = 0;
     for (int j = 0; j < m; ++j) {
+        if ((j & 31) == 0) {
+            lb = le = 0;
+            const int jl = j + static_cast<int>(lane);
+            if (jl < m) lookup_bucket(tables[jl], substring_bits<W>(g, tables[jl].off, tables[jl].len), lb, le);
+        }
         const TableDesc& t = tables[j];
-        uint32_t b = 0, e = 0;
-        if (lane == 0) lookup_bucket(t, substring_bits<W>(g, t.off, t.len), b, e);
-        b = __shfl_sync(0xFFFFFFFFu, b, 0);
-        e = __shfl_sync(0xFFFFFFFFu, e, 0);
+        const uint32_t b = __shfl_sync(0xFFFFFFFFu, lb, j & 31);
+        const uint32_t e = __shfl_sync(0xFFFFFFFFu, le, j & 31);
         const uint32_t end = min(e, b + probe);
         if (t.codes && t.rec_words != 0) {
             // Inline records (every substring one 32-bit word): the table's own
@@ -1764,16 +1772,28 @@ __global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __res
 #pragma unroll
             for (int i = 0; i < R; ++i) gq[i] = i < j ? g32[i] : g32[i + 1];
             const uint32_t* rec = reinterpret_cast<const uint32_t*>(t.codes);
-            for (uint32_t p = b + lane; p < end; p += 32) {
-                int d = 0;
-                bool first = true;
+            // kProbeBatch records per lane per round, their loads in flight together
+            for (uint64_t p0 = b; p0 < end; p0 += 32u * kProbeBatch) {
+                uint32_t wv[kProbeBatch][R];
 #pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const uint32_t x = __ldg(rec + static_cast<uint64_t>(p) * R + i) ^ gq[i];
-                    d += __popc(x);
-                    if (i < j && x == 0u) first = false;
+                for (int u = 0; u < kProbeBatch; ++u) {
+                    const uint64_t p = p0 + 32u * u + lane;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) wv[u][i] = p < end ? __ldg(rec + p * R + i) : 0u;
                 }
-                if (first) atomicAdd(&h[d], 1u);
+#pragma unroll
+                for (int u = 0; u < kProbeBatch; ++u) {
+                    if (p0 + 32u * u + lane >= end) continue;
+                    int d = 0;
+                    bool first = true;
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        const uint32_t x = wv[u][i] ^ gq[i];
+                        d += __popc(x);
+                        if (i < j && x == 0u) first = false;
+                    }
+                    if (first) atomicAdd(&h[d], 1u);
+                }
             }
             continue;
         }
