@@ -113,14 +113,28 @@ __device__ __forceinline__ uint32_t substring_bits(const Code<W>& c, int off, in
 // rho-subsets of {0..s-1} in increasing numeric order (colex order), so a
 // rank maps to a subset by the combinatorial number system and consecutive
 // ranks are one Gosper step apart.
+// The element c_i of each position is the largest c below the previous one
+// with C(c, i) <= rank: found by binary search (C(c, i) grows with c), and
+// for i = 1 it is the rank itself.
 __device__ __forceinline__ uint64_t unrank_subset(uint64_t rank, int s, int rho) {
     uint64_t x = 0;
-    int c = s;
+    int hi = s;   // c < hi
     for (int i = rho; i >= 1; --i) {
-        --c;
-        while (binom(c, i) > rank) --c;
+        int c;
+        if (i == 1) {
+            c = static_cast<int>(rank);
+        } else {
+            int lo = i - 1, h = hi - 1;
+            while (lo < h) {
+                const int mid = (lo + h + 1) >> 1;
+                if (binom(mid, i) <= rank) lo = mid;
+                else h = mid - 1;
+            }
+            c = lo;
+        }
         rank -= binom(c, i);
         x |= 1ull << c;
+        hi = c;
     }
     return x;
 }

@@ -1317,8 +1317,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_scan_kernel(const TableDesc
 
 // The same planning from per-query chunk counts that the stopping test wrote
 // for this wave: an exclusive scan of `counts` into chunk_off[0..nq], in
-// tiles of four counts per thread (coalesced loads), and the zeroed work
-// counters.  One CTA.
+// tiles of sixteen counts per thread, and the zeroed work counters.  One CTA.
 __global__ void __launch_bounds__(kPlanThreads) plan_counts_kernel(const uint32_t* __restrict__ counts, uint32_t nq,
                                                                    uint64_t* __restrict__ chunk_off,
                                                                    unsigned long long* __restrict__ counters) {
@@ -1327,13 +1326,30 @@ __global__ void __launch_bounds__(kPlanThreads) plan_counts_kernel(const uint32_
     if (threadIdx.x < 2) counters[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) s_carry = 0ull;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    constexpr uint32_t kTile = 4u * kPlanThreads;
+    // kPer counts per thread: up to 16K queries are one tile, every load in
+    // flight at once (16-byte loads where the counts are 16-byte aligned)
+    constexpr int kPer = 16;
+    constexpr uint32_t kTile = kPer * kPlanThreads;
+    const bool vec = (reinterpret_cast<uintptr_t>(counts) & 15u) == 0;
     for (uint32_t base = 0; base < nq; base += kTile) {
-        const uint32_t i0 = base + 4u * threadIdx.x;
-        uint32_t c[4];
+        const uint32_t i0 = base + kPer * threadIdx.x;
+        uint32_t c[kPer];
+        if (vec && i0 + kPer <= nq) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) c[r] = i0 + r < nq ? __ldg(counts + i0 + r) : 0u;
-        const unsigned long long sum = static_cast<unsigned long long>(c[0]) + c[1] + c[2] + c[3];
+            for (int r = 0; r < kPer; r += 4) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(counts + i0 + r));
+                c[r] = v.x;
+                c[r + 1] = v.y;
+                c[r + 2] = v.z;
+                c[r + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) c[r] = i0 + r < nq ? __ldg(counts + i0 + r) : 0u;
+        }
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) sum += c[r];
         unsigned long long incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1355,7 +1371,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_counts_kernel(const uint32_
         __syncthreads();
         unsigned long long run = s_carry + (warp > 0 ? s_warp[warp - 1] : 0ull) + incl - sum;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < kPer; ++r) {
             if (i0 + r < nq) chunk_off[i0 + r] = run;
             run += c[r];
         }
