@@ -81,7 +81,7 @@ typedef struct {
     int32_t probe;         /* Before the first step, measure up to `probe` entries
                               of each query's own bucket in every table to get a
                               first bound on its k-th distance (results
-                              unchanged).  0 = default (1024), negative = off. */
+                              unchanged).  0 = default (4096), negative = off. */
     int32_t executor;      /* How mih_knn runs its waves of Alg. 3 steps (results
                               unchanged): MIH_EXEC_GRAPH = one CUDA graph whose
                               while-loop node repeats the wave and its stopping

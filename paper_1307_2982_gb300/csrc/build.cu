@@ -395,7 +395,7 @@ mih_status mih_build(const uint64_t* codes, uint64_t n, int q, int m, const mih_
     ix->n = n;
     ix->codes = codes;
     ix->scan_factor = params ? params->scan_factor : 0;
-    ix->probe = (!params || params->probe == 0) ? 1024 : (params->probe < 0 ? 0 : params->probe);
+    ix->probe = (!params || params->probe == 0) ? 4096 : (params->probe < 0 ? 0 : params->probe);
     ix->executor = params ? params->executor : MIH_EXEC_AUTO;
     ix->tail_from = (!params || params->tail_from <= 0) ? -1 : params->tail_from;
     ix->slice_shape = params ? params->slice_shape : MIH_SLICE_SHAPE_3K_8W;
