@@ -1741,7 +1741,10 @@ __global__ void init_knn_kernel(uint32_t nq, uint64_t n, int32_t* t_lo, int32_t*
 // least min(k, n) probed codes within D is a valid bound; queries that probe
 // fewer codes keep bound = -1 (histogram-only steps until one exists).
 
-constexpr int kProbeBatch = 8;   // records per lane in flight in the bound probe
+#ifndef MIH_PROBE_BATCH
+#define MIH_PROBE_BATCH 8
+#endif
+constexpr int kProbeBatch = MIH_PROBE_BATCH;   // records per lane in flight in the bound probe
 
 template <int W>
 __global__ void __launch_bounds__(256) bound_probe_kernel(const TableDesc* __restrict__ tables, int m, int qbits,
