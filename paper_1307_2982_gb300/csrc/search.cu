@@ -1400,38 +1400,23 @@ __device__ __forceinline__ uint32_t kk_of(const uint32_t* kq, uint32_t k_uniform
 // min(k, n) codes are known the bound (an upper bound on the k-th distance)
 // exists; the next launch then revisits steps 0..t to store the codes within
 // the bound (without counting them again) together with step t+1.
-//
-// One warp per query, 8 queries per CTA.  With chunk_off given, the kernel
-// also plans the next wave: the exclusive scan of the next chunk counts into
-// chunk_off[0..nq], in one pass over the CTAs (each publishes its own sum in
-// tiles[b], then adds its predecessors' sums, waiting for each within the
-// bounded-wait limit, until one has published its running total), and the
-// zeroed work counters.  An expired wait raises *timeout (the call then
-// fails with MIH_ETIMEOUT).  tiles[] starts at zero every wave.
-constexpr int kStopQueries = 8;   // queries (warps) per CTA of the stopping test
-constexpr unsigned long long kTileSum = 1ull << 62, kTileRun = 2ull << 62, kTileMask = kTileSum - 1;
-
-__global__ void __launch_bounds__(kStopQueries * 32)
-    knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32_t* __restrict__ kq, uint32_t k_uniform,
-                    const uint32_t* __restrict__ hist, int32_t* __restrict__ t_lo, int32_t* __restrict__ t_hi,
-                    int32_t* __restrict__ bound, int32_t* __restrict__ dk, int32_t* __restrict__ hist_done,
-                    uint32_t* __restrict__ cnt1, uint32_t cap, unsigned long long* __restrict__ qstats,
-                    unsigned int* __restrict__ active, const TableDesc* __restrict__ tables, int m,
-                    uint8_t* __restrict__ exh, long long scan_budget, uint32_t* __restrict__ next_chunks,
-                    int tail_from, uint64_t* __restrict__ chunk_off, unsigned long long* __restrict__ counters,
-                    unsigned long long* __restrict__ tiles, int* __restrict__ timeout, uint64_t wait_ns) {
+__global__ void knn_stop_kernel(uint32_t nq, int qbits, uint64_t n, const uint32_t* __restrict__ kq,
+                                uint32_t k_uniform, const uint32_t* __restrict__ hist, int32_t* __restrict__ t_lo,
+                                int32_t* __restrict__ t_hi, int32_t* __restrict__ bound, int32_t* __restrict__ dk,
+                                int32_t* __restrict__ hist_done, uint32_t* __restrict__ cnt1, uint32_t cap,
+                                unsigned long long* __restrict__ qstats, unsigned int* __restrict__ active,
+                                const TableDesc* __restrict__ tables, int m, uint8_t* __restrict__ exh,
+                                long long scan_budget, uint32_t* __restrict__ next_chunks, int tail_from) {
     __shared__ int s_len[kMaxTables];
-    __shared__ uint32_t s_cnt[kStopQueries];
     for (int j = threadIdx.x; j < m; j += blockDim.x) s_len[j] = tables[j].len;
-    if (threadIdx.x < kStopQueries) s_cnt[threadIdx.x] = 0u;
-    if (chunk_off && blockIdx.x == 0 && threadIdx.x < 2) counters[threadIdx.x] = 0ull;
     __syncthreads();
-    // lane l sums bins [l * per, (l + 1) * per)
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    // one warp per query: lane l sums bins [l * per, (l + 1) * per)
+    const uint32_t lane = lane_id();
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     const int per = (qbits + 1 + 31) / 32;
-    const uint32_t q = blockIdx.x * kStopQueries + warp;
-    if (q < nq && t_hi[q] >= t_lo[q]) {   // (a query retired earlier has no chunks)
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
         const int t = t_hi[q];
+        if (t < t_lo[q]) continue;  // retired earlier (warp-uniform)
         const uint32_t kk = kk_of(kq, k_uniform, q, n);
         const uint32_t* h = hist + static_cast<uint64_t>(q) * (qbits + 1);
         const int d0 = static_cast<int>(lane) * per;
@@ -1450,80 +1435,39 @@ __global__ void __launch_bounds__(kStopQueries * 32)
         }
         const uint32_t who = __ballot_sync(0xFFFFFFFFu, reach >= 0);
         const int first_reach = who ? __shfl_sync(0xFFFFFFFFu, reach, __ffs(who) - 1) : -1;
-        if (lane == 0) {
-            const bool full = exh[q] != 0;  // this launch verified every remaining code
-            if (first_reach >= 0 && (first_reach <= t || full)) {
-                dk[q] = first_reach;            // every code within t bits (or all codes) is known
-                t_lo[q] = t + 1;
-                qstats[4ull * q + 3] = static_cast<unsigned long long>(t);
-                if (bound[q] < 0) cnt1[q] = cap + 1;  // nothing stored yet: second pass collects
-                next_chunks[q] = 0u;
+        if (lane != 0) continue;
+        const bool full = exh[q] != 0;  // this launch verified every remaining code
+        if (first_reach >= 0 && (first_reach <= t || full)) {
+            dk[q] = first_reach;            // every code within t bits (or all codes) is known
+            t_lo[q] = t + 1;
+            qstats[4ull * q + 3] = static_cast<unsigned long long>(t);
+            if (bound[q] < 0) cnt1[q] = cap + 1;  // nothing stored yet: second pass collects
+            next_chunks[q] = 0u;
+        } else {
+            hist_done[q] = t;
+            if (bound[q] < 0 && first_reach >= 0) {
+                bound[q] = first_reach;
+                t_lo[q] = 0;                // revisit steps 0..t to store under the new bound
             } else {
-                hist_done[q] = t;
-                if (bound[q] < 0 && first_reach >= 0) {
-                    bound[q] = first_reach;
-                    t_lo[q] = 0;                // revisit steps 0..t to store under the new bound
-                } else {
-                    if (first_reach >= 0 && (bound[q] < 0 || first_reach < bound[q])) bound[q] = first_reach;
-                    t_lo[q] = t + 1;
-                }
-                // one Alg. 3 step per wave, two from step tail_from on (every code
-                // within t bits is known after steps 0..t, so the next stopping
-                // test is exact either way)
-                const int steps = (tail_from >= 0 && t + 1 >= tail_from) ? 2 : 1;
-                t_hi[q] = t + steps;
-                // Once the next steps alone would push the lookups past the budget,
-                // verifying every remaining code once is cheaper (Sec. 3 cost model:
-                // a lookup costs about one candidate test).
-                if (scan_budget >= 0 && qstats[4ull * q] + steps_lookups(s_len, m, t + 1, t + steps) >
-                                            static_cast<unsigned long long>(scan_budget))
-                    exh[q] = 1;
-                // chunks of the next wave's steps, for its planning
-                const uint32_t c = static_cast<uint32_t>(query_chunks(s_len, m, n, t_lo, t_hi, exh, q));
-                next_chunks[q] = c;
-                s_cnt[warp] = c;
-                atomicAdd(active, 1u);
+                if (first_reach >= 0 && (bound[q] < 0 || first_reach < bound[q])) bound[q] = first_reach;
+                t_lo[q] = t + 1;
             }
+            // one Alg. 3 step per wave, two from step tail_from on (every code
+            // within t bits is known after steps 0..t, so the next stopping
+            // test is exact either way)
+            const int steps = (tail_from >= 0 && t + 1 >= tail_from) ? 2 : 1;
+            t_hi[q] = t + steps;
+            // Once the next steps alone would push the lookups past the budget,
+            // verifying every remaining code once is cheaper (Sec. 3 cost model:
+            // a lookup costs about one candidate test).
+            if (scan_budget >= 0 &&
+                qstats[4ull * q] + steps_lookups(s_len, m, t + 1, t + steps) > static_cast<unsigned long long>(scan_budget))
+                exh[q] = 1;
+            // chunks of the next wave's steps, for its planning
+            next_chunks[q] = static_cast<uint32_t>(query_chunks(s_len, m, n, t_lo, t_hi, exh, q));
+            atomicAdd(active, 1u);
         }
     }
-    if (chunk_off == nullptr) return;   // (uniform over the grid)
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    unsigned long long loc[kStopQueries], sum = 0;
-#pragma unroll
-    for (int w = 0; w < kStopQueries; ++w) {
-        loc[w] = sum;
-        sum += s_cnt[w];
-    }
-    const uint32_t b = blockIdx.x;
-    unsigned long long before = 0;
-    if (b == 0) {
-        atomicExch(tiles, kTileRun | sum);
-    } else {
-        atomicExch(tiles + b, kTileSum | sum);
-        const uint64_t t0 = global_ns();
-        for (int64_t p = static_cast<int64_t>(b) - 1; p >= 0;) {
-            const unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(tiles + p);
-            if (v == 0ull) {   // not published yet
-                if (global_ns() - t0 > wait_ns) {
-                    atomicExch(timeout, 1);
-                    break;
-                }
-                __nanosleep(64);
-                continue;
-            }
-            before += v & kTileMask;
-            if (v & kTileRun) break;   // its running total covers every earlier CTA
-            --p;
-        }
-        atomicExch(tiles + b, kTileRun | (before + sum));
-    }
-#pragma unroll
-    for (int w = 0; w < kStopQueries; ++w) {
-        const uint32_t qw = b * kStopQueries + w;
-        if (qw < nq) chunk_off[qw] = before + loc[w];
-    }
-    if (b == gridDim.x - 1) chunk_off[nq] = before + sum;
 }
 
 // Loop control of the graph executor, after the stopping test of a wave:
@@ -2092,10 +2036,15 @@ mih_status check_timeout(const Plan& p, cudaStream_t s) {
     return MIH_OK;
 }
 
-// Chunk offsets of the current step ranges (chunk_off) and zeroed work
-// counters, on stream s (a capture stream when in_graph).
-mih_status plan_wave(const mih_index* ix, const SearchArgs& a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
-                     Workspace& ws, cudaStream_t s, bool in_graph, const uint32_t* counts) {
+// Compute chunk offsets for the current step ranges and run one search launch.
+// With a capture stream cs the launches are recorded into a graph body on cs
+// (nothing is allocated and no event is recorded); else they run on the
+// workspace's stream.
+template <int MODE>
+mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
+                    const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr, const uint32_t* counts = nullptr) {
+    const bool in_graph = cs != nullptr;
+    cudaStream_t s = in_graph ? cs : ws.stream();
     {
         KernelSpan plan_span(s, MIH_PROF_PLAN, !in_graph);
         if (counts && static_cast<uint64_t>(a.nq) + 1 <= kPlanOneBlockMax) {
@@ -2117,21 +2066,6 @@ mih_status plan_wave(const mih_index* ix, const SearchArgs& a, Plan& p, const in
             MIH_CUDA(cudaMemsetAsync(p.counters, 0, 2 * sizeof(unsigned long long), s));
         }
     }
-    return MIH_OK;
-}
-
-// Run one search launch over the current step ranges, after computing their
-// chunk offsets unless `planned` (the stopping test of the previous wave wrote
-// them).  With a capture stream cs the launches are recorded into a graph
-// body on cs (nothing is allocated and no event is recorded); else they run
-// on the workspace's stream.
-template <int MODE>
-mih_status run_wave(const mih_index* ix, SearchArgs a, Plan& p, const int32_t* t_lo, const int32_t* t_hi,
-                    const DeviceInfo& dev, Workspace& ws, cudaStream_t cs = nullptr, const uint32_t* counts = nullptr,
-                    bool planned = false) {
-    const bool in_graph = cs != nullptr;
-    cudaStream_t s = in_graph ? cs : ws.stream();
-    if (!planned) MIH_TRY(plan_wave(ix, a, p, t_lo, t_hi, ws, s, in_graph, counts));
     a.t_lo = t_lo;
     a.t_hi = t_hi;
     a.chunk_off = p.chunk_off;
@@ -2474,12 +2408,7 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
     MIH_TRY(ws.alloc(&cnt1, nq));
     MIH_TRY(ws.alloc(&buf1, static_cast<size_t>(nq) * cap));
     MIH_TRY(ws.alloc(&qstats, 4ull * nq));
-    // the active count, then one running-total tile per CTA of the stopping
-    // test (its planning scan), cleared together before every test
-    const uint32_t stop_ctas = (nq + kStopQueries - 1) / kStopQueries;
-    unsigned long long* stopbuf;
-    MIH_TRY(ws.alloc(&stopbuf, 1 + static_cast<size_t>(stop_ctas)));
-    active = reinterpret_cast<unsigned int*>(stopbuf);
+    MIH_TRY(ws.alloc(&active, 1));
     unsigned long long* sliced;
     MIH_TRY(ws.alloc(&sliced, 1));
     MIH_CUDA(cudaMemsetAsync(sliced, 0, sizeof(unsigned long long), s));
@@ -2537,19 +2466,14 @@ mih_status mih_knn(const mih_index* ix, const uint64_t* queries, uint32_t nq, co
 
     // One wave: every active query runs its current Alg. 3 step(s), then the
     // stopping test advances or retires it.  cs = capture stream (graph) or 0.
-    // The first wave's chunk offsets come from here; every stopping test then
-    // plans the next wave itself.
-    if (ix->n > 0) MIH_TRY(plan_wave(ix, a, plan, t_lo, t_hi, ws, s, false, wave_chunks));
-    const uint64_t wait_ns = wait_limit_ns();
     auto wave = [&](cudaStream_t cs) -> mih_status {
         cudaStream_t ws_s = cs ? cs : s;
-        MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs, wave_chunks, true));
-        MIH_CUDA(cudaMemsetAsync(stopbuf, 0, sizeof(unsigned long long) * (1 + static_cast<size_t>(stop_ctas)), ws_s));
+        MIH_TRY(run_wave<kModeKnn>(ix, a, plan, t_lo, t_hi, dev, ws, cs, wave_chunks));
+        MIH_CUDA(cudaMemsetAsync(active, 0, sizeof(unsigned int), ws_s));
         KernelSpan ks(ws_s, MIH_PROF_STOP, cs == nullptr);
-        knn_stop_kernel<<<stop_ctas, kStopQueries * 32, 0, ws_s>>>(
-            nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk, hist_done, cnt1, cap, qstats, active,
-            ix->dev_tables, ix->m, exh, budget, wave_chunks, query_stats ? -1 : ix->tail_from, plan.chunk_off,
-            plan.counters, stopbuf + 1, plan.timeout, wait_ns);
+        knn_stop_kernel<<<grid1(32ull * nq), 256, 0, ws_s>>>(nq, qb, ix->n, k, k_uniform, hist, t_lo, t_hi, bound, dk,
+                                                    hist_done, cnt1, cap, qstats, active, ix->dev_tables, ix->m,
+                                                    exh, budget, wave_chunks, query_stats ? -1 : ix->tail_from);
         MIH_LAUNCH_CHECK();
         return MIH_OK;
     };
