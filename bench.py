@@ -597,8 +597,8 @@ def run_ours(a):
         r_ms /= reps
         cands = int((out_ids != -1).sum().item())
         sectors_gbs = cands * 32 / (r_ms / 1e3) / 1e9
-        rerank = {"k_in": k, "k": ko, "queries": nq, "kernel": "rerank_asym_kernel (one CTA per query, fp64 sums, "
-                  "bitonic sort in shared memory)", "kernel_ms": r_ms, "call_ms": r_call / reps,
+        rerank = {"k_in": k, "k": ko, "queries": nq, "kernel": "rerank_warp_kernel (one warp per row, exact integer sums on the "
+                  "query's fixed-point grid, bitonic sort by shuffles)", "kernel_ms": r_ms, "call_ms": r_call / reps,
                   "candidates_per_s": cands / (r_ms / 1e3),
                   "roofline": {"bound": "gather", "achieved": sectors_gbs, "unit": "GB/s",
                                "peak": ceilings["gather32_gbs"], "frac": sectors_gbs / ceilings["gather32_gbs"],
