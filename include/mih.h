@@ -330,6 +330,25 @@ MIH_API mih_status mih_rerank_asym(const uint64_t *codes, uint64_t n, int q, con
                                    const uint32_t *ids, uint32_t k_in, uint32_t k, uint32_t *out_ids,
                                    double *out_a, void *stream);
 
+/* mih_rerank_asym for rows of different lengths (e.g. mih_knn's answers
+ * for a per-query k, with their CSR offsets): row i's candidates are
+ * ids[in_offsets[i] .. in_offsets[i+1]) and its results go to
+ * out_ids / out_a [out_offsets[i] .. out_offsets[i+1]), the first
+ * out_offsets[i+1] - out_offsets[i] entries of the row in (a, id) order,
+ * padded as in mih_rerank_asym.  in_offsets, out_offsets: device
+ * uint64[nq + 1], non-decreasing.  k_in_max: the longest candidate row,
+ * 1 <= k_in_max <= MIH_MAX_K (it sizes the sort); every result row at most
+ * MIH_MAX_K.  Other arguments, the distance and the synchronisation as in
+ * mih_rerank_asym.
+ * Errors: MIH_EINVAL (as mih_rerank_asym, and a row longer than k_in_max or
+ * MIH_MAX_K, or decreasing offsets: the outputs are then unspecified),
+ * MIH_ENOMEM, MIH_ECUDA.
+ */
+MIH_API mih_status mih_rerank_asym_csr(const uint64_t *codes, uint64_t n, int q, const float *proj, uint32_t nq,
+                                       const uint32_t *ids, const uint64_t *in_offsets, uint32_t k_in_max,
+                                       const uint64_t *out_offsets, uint32_t *out_ids, double *out_a,
+                                       void *stream);
+
 /* ------------------------------------------------------------------------
  * mih_set_scan_kernel -- which kernel linscan_knn uses for calls from the
  * calling host thread (results are identical):

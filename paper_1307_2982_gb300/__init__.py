@@ -37,7 +37,7 @@ EXPORTS = (
     "mih_last_error", "mih_version", "mih_set_timing", "mih_last_profile", "linscan_knn_noalloc",
     "mih_autotune", "mih_greedy_substrings", "mih_bit_correlation", "mih_set_wait_limit",
     "mih_cost_layout", "mih_autotune_layout", "mih_merge_topk", "mih_measure_ceilings",
-    "mih_set_scan_kernel", "mih_k_offsets", "mih_tune_search", "mih_rerank_asym",
+    "mih_set_scan_kernel", "mih_k_offsets", "mih_tune_search", "mih_rerank_asym", "mih_rerank_asym_csr",
 )
 
 
@@ -147,6 +147,8 @@ def load():
     lib.mih_merge_topk.restype = st
     lib.mih_rerank_asym.argtypes = [P, u64, i32, P, u32, P, u32, u32, P, P, P]
     lib.mih_rerank_asym.restype = st
+    lib.mih_rerank_asym_csr.argtypes = [P, u64, i32, P, u32, P, P, u32, P, P, P, P]
+    lib.mih_rerank_asym_csr.restype = st
     lib.mih_suggest_m.argtypes = [i32, u64]
     lib.mih_suggest_m.restype = i32
     lib.mih_status_str.argtypes = [st]
@@ -566,6 +568,39 @@ def mih_rerank_asym(codes, q: int, proj, ids, k: int, stream=None, out=None):
     _check(load().mih_rerank_asym(cptr, n, q, _ptr(proj), nq, _ptr(ids), k_in, k, _ptr(oi), _ptr(oa),
                                   _stream(stream)), "mih_rerank_asym")
     return {"ids": oi, "a": oa}
+
+
+def mih_rerank_asym_csr(codes, q: int, proj, ids, in_offsets, out_offsets, k_in_max: int | None = None,
+                        stream=None, out=None):
+    """mih_rerank_asym for CSR rows: row i's candidates are
+    ids[in_offsets[i]:in_offsets[i+1]] (CUDA int32 / uint32 bit patterns, -1 =
+    padding), its results out[out_offsets[i]:out_offsets[i+1]].  Offsets:
+    (nq + 1,) CUDA int64.  k_in_max: the longest candidate row (read from
+    in_offsets when None).  Returns {"ids": int32, "a": float64}, flat."""
+    import torch
+
+    cptr, n = _codes_arg(codes, q)
+    if not (proj.is_cuda and ids.is_cuda and in_offsets.is_cuda and out_offsets.is_cuda):
+        raise ValueError("proj, ids and the offsets must be CUDA tensors")
+    if proj.dtype != torch.float32 or proj.dim() != 2 or proj.shape[1] != q or not proj.is_contiguous():
+        raise ValueError(f"proj must be a contiguous (nq, {q}) float32 tensor")
+    nq = proj.shape[0]
+    for t in (in_offsets, out_offsets):
+        if t.dim() != 1 or t.shape[0] != nq + 1 or t.element_size() != 8 or not t.is_contiguous():
+            raise ValueError("offsets must be contiguous (nq + 1,) tensors of 8-byte integers")
+    if ids.element_size() != 4 or not ids.is_contiguous():
+        raise ValueError("ids must be a contiguous tensor of 4-byte ids")
+    if k_in_max is None:
+        k_in_max = int((in_offsets[1:] - in_offsets[:-1]).max().item()) if nq > 0 else 1
+    total = int(out_offsets[-1].item()) if nq > 0 else 0
+    if out is None:
+        oi = torch.empty(max(total, 1), dtype=torch.int32, device=ids.device)
+        oa = torch.empty(max(total, 1), dtype=torch.float64, device=ids.device)
+    else:
+        oi, oa = out
+    _check(load().mih_rerank_asym_csr(cptr, n, q, _ptr(proj), nq, _ptr(ids), _ptr(in_offsets), max(k_in_max, 1),
+                                      _ptr(out_offsets), _ptr(oi), _ptr(oa), _stream(stream)), "mih_rerank_asym_csr")
+    return {"ids": oi[:total], "a": oa[:total]}
 
 
 def mih_knn_asym(index, codes, queries, proj, k: int, k_candidates: int, stream=None):

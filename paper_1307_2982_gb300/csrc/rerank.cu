@@ -35,8 +35,42 @@ struct RerankArgs {
     uint32_t k_in, k, P;  // P: power of two >= k_in, the sort width
     uint32_t* out_ids;    // [nq][k]
     double* out_a;
-    unsigned int* bad;    // set when a candidate id is >= n
+    unsigned int* bad;    // bit 0: a candidate id >= n; bit 1: a row longer than k_in;
+                          // bit 2: a result row longer than MIH_MAX_K
+    const uint64_t* in_off;    // CSR rows (nullable: uniform rows of k_in)
+    const uint64_t* out_off;   // CSR results (nullable: uniform rows of k)
 };
+
+// Row `row`'s candidates ids[ib, ib + len) and result slots [ob, ob + kr).
+struct RowSpan {
+    uint64_t ib, ob;
+    uint32_t len, kr;
+};
+
+__device__ __forceinline__ RowSpan row_span(const RerankArgs& a, uint64_t row, bool report) {
+    RowSpan r;
+    if (a.in_off) {
+        r.ib = a.in_off[row];
+        const uint64_t e = a.in_off[row + 1];
+        const bool over = e < r.ib || e - r.ib > a.k_in;
+        if (over && report) atomicOr(a.bad, 2u);
+        r.len = over ? 0u : static_cast<uint32_t>(e - r.ib);
+    } else {
+        r.ib = row * a.k_in;
+        r.len = a.k_in;
+    }
+    if (a.out_off) {
+        r.ob = a.out_off[row];
+        const uint64_t e = a.out_off[row + 1];
+        const bool over = e < r.ob || e - r.ob > MIH_MAX_K;
+        if (over && report) atomicOr(a.bad, 4u);
+        r.kr = over ? 0u : static_cast<uint32_t>(e - r.ob);
+    } else {
+        r.ob = row * a.k;
+        r.kr = a.k;
+    }
+    return r;
+}
 
 // Shared memory of a row: sort keys (the integer sums), the weights, the
 // sign code, ids, and the row's largest |y_b| (as its fp32 bit pattern).
@@ -60,6 +94,7 @@ __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
     uint32_t* ymax = cid + a.P;        // largest |y_b|, fp32 bits (nonnegative: they order as integers)
 
     const uint64_t row = blockIdx.x;
+    const RowSpan rs = row_span(a, row, threadIdx.x == 0);
     const float* y = a.proj + row * (64 * W);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
     if (threadIdx.x == 0) *ymax = 0u;
@@ -88,8 +123,8 @@ __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
     for (uint32_t i = threadIdx.x; i < a.P; i += blockDim.x) {
         uint64_t kk = ~0ull;
         uint32_t id = kPadId;
-        if (i < a.k_in) {
-            id = __ldg(a.ids + row * a.k_in + i);
+        if (i < rs.len) {
+            id = __ldg(a.ids + rs.ib + i);
             if (id != kPadId && id >= a.n) {
                 atomicOr(a.bad, 1u);
                 id = kPadId;
@@ -133,10 +168,10 @@ __global__ void __launch_bounds__(512) rerank_asym_kernel(RerankArgs a) {
     }
     __syncthreads();
 
-    for (uint32_t p = threadIdx.x; p < a.k; p += blockDim.x) {
+    for (uint32_t p = threadIdx.x; p < rs.kr; p += blockDim.x) {
         const bool real = p < a.P && key[p] != ~0ull;
-        a.out_ids[row * a.k + p] = real ? cid[p] : kPadId;
-        a.out_a[row * a.k + p] = real ? __ull2double_rn(key[p]) * pow2(-s) : -1.0;
+        a.out_ids[rs.ob + p] = real ? cid[p] : kPadId;
+        a.out_a[rs.ob + p] = real ? __ull2double_rn(key[p]) * pow2(-s) : -1.0;
     }
 }
 
@@ -163,6 +198,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) rerank_warp_kernel(RerankArgs 
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t row = static_cast<uint64_t>(blockIdx.x) * kRowWarps + warp;
     if (row >= nq) return;   // warp-uniform; the kernel has no block barrier
+    const RowSpan rs = row_span(a, row, threadIdx.x % 32 == 0);
     uint64_t* wt = s_wt[warp];
     const float* y = a.proj + row * (64 * W);
 
@@ -191,7 +227,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) rerank_warp_kernel(RerankArgs 
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const uint32_t x = 32u * e + lane;
-        cid[e] = x < a.k_in ? __ldg(a.ids + row * a.k_in + x) : kPadId;
+        cid[e] = x < rs.len ? __ldg(a.ids + rs.ib + x) : kPadId;
         if (cid[e] != kPadId && cid[e] >= a.n) {
             atomicOr(a.bad, 1u);
             cid[e] = kPadId;
@@ -256,15 +292,15 @@ __global__ void __launch_bounds__(kRowWarps * 32) rerank_warp_kernel(RerankArgs 
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const uint32_t x = 32u * e + lane;
-        if (x < a.k) {
+        if (x < rs.kr) {
             const bool real = key[e] != ~0ull;
-            a.out_ids[row * a.k + x] = real ? cid[e] : kPadId;
-            a.out_a[row * a.k + x] = real ? __ull2double_rn(key[e]) * unscale : -1.0;
+            a.out_ids[rs.ob + x] = real ? cid[e] : kPadId;
+            a.out_a[rs.ob + x] = real ? __ull2double_rn(key[e]) * unscale : -1.0;
         }
     }
-    for (uint32_t x = 32u * E + lane; x < a.k; x += 32) {
-        a.out_ids[row * a.k + x] = kPadId;
-        a.out_a[row * a.k + x] = -1.0;
+    for (uint32_t x = 32u * E + lane; x < rs.kr; x += 32) {
+        a.out_ids[rs.ob + x] = kPadId;
+        a.out_a[rs.ob + x] = -1.0;
     }
 }
 
@@ -307,37 +343,43 @@ mih_status launch_rerank(const RerankArgs& a, uint32_t nq, cudaStream_t s) {
 }  // namespace
 }  // namespace mih
 
-extern "C" mih_status mih_rerank_asym(const uint64_t* codes, uint64_t n, int q, const float* proj, uint32_t nq,
-                                      const uint32_t* ids, uint32_t k_in, uint32_t k, uint32_t* out_ids,
-                                      double* out_a, void* stream) {
-    using namespace mih;
+namespace mih {
+namespace {
+
+// The checks and the launch shared by both entry points (`name` prefixes
+// error messages).  in_off / out_off null: uniform rows of k_in / k.
+mih_status rerank_call(const char* name, const uint64_t* codes, uint64_t n, int q, const float* proj, uint32_t nq,
+                       const uint32_t* ids, const uint64_t* in_off, uint32_t k_in, const uint64_t* out_off,
+                       uint32_t k, uint32_t* out_ids, double* out_a, void* stream) {
     clear_error();
     if (q != 64 && q != 128 && q != 256) {
-        set_error("mih_rerank_asym: q must be 64, 128 or 256 (got %d)", q);
+        set_error("%s: q must be 64, 128 or 256 (got %d)", name, q);
         return MIH_EINVAL;
     }
     if (n >= 0xFFFFFFFFull) {
-        set_error("mih_rerank_asym: n must be below 2^32 - 1");
+        set_error("%s: n must be below 2^32 - 1", name);
         return MIH_EINVAL;
     }
-    if (k_in < 1 || k_in > MIH_MAX_K || k < 1 || k > MIH_MAX_K) {
-        set_error("mih_rerank_asym: k_in and k must be in [1, %u]", MIH_MAX_K);
+    if (k_in < 1 || k_in > MIH_MAX_K || (out_off == nullptr && (k < 1 || k > MIH_MAX_K))) {
+        set_error("%s: k_in and k must be in [1, %u]", name, MIH_MAX_K);
         return MIH_EINVAL;
     }
     if (nq > (1u << 23)) {
-        set_error("mih_rerank_asym: nq must be at most 2^23");
+        set_error("%s: nq must be at most 2^23", name);
         return MIH_EINVAL;
     }
     if (nq == 0) return MIH_OK;
     const int W = q / 64;
     if (n > 0) {
-        MIH_TRY(check_device_ptr(codes, "mih_rerank_asym: codes"));
-        MIH_TRY(check_code_alignment(codes, W, "mih_rerank_asym: codes"));
+        MIH_TRY(check_device_ptr(codes, "rerank: codes"));
+        MIH_TRY(check_code_alignment(codes, W, "rerank: codes"));
     }
-    MIH_TRY(check_device_ptr(proj, "mih_rerank_asym: proj"));
-    MIH_TRY(check_device_ptr(ids, "mih_rerank_asym: ids"));
-    MIH_TRY(check_device_ptr(out_ids, "mih_rerank_asym: out_ids"));
-    MIH_TRY(check_device_ptr(out_a, "mih_rerank_asym: out_a"));
+    MIH_TRY(check_device_ptr(proj, "rerank: proj"));
+    MIH_TRY(check_device_ptr(ids, "rerank: ids"));
+    MIH_TRY(check_device_ptr(out_ids, "rerank: out_ids"));
+    MIH_TRY(check_device_ptr(out_a, "rerank: out_a"));
+    if (in_off) MIH_TRY(check_device_ptr(in_off, "rerank: in_offsets"));
+    if (out_off) MIH_TRY(check_device_ptr(out_off, "rerank: out_offsets"));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CallScope scope(s);
     Workspace ws(s);
@@ -357,15 +399,48 @@ extern "C" mih_status mih_rerank_asym(const uint64_t* codes, uint64_t n, int q, 
     a.out_ids = out_ids;
     a.out_a = out_a;
     a.bad = bad;
+    a.in_off = in_off;
+    a.out_off = out_off;
     if (W == 1) MIH_TRY(launch_rerank<1>(a, nq, s));
     else if (W == 2) MIH_TRY(launch_rerank<2>(a, nq, s));
     else MIH_TRY(launch_rerank<4>(a, nq, s));
     unsigned int hbad = 0;
     MIH_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     MIH_CUDA(cudaStreamSynchronize(s));
-    if (hbad) {
-        set_error("mih_rerank_asym: a candidate id is >= n (0xFFFFFFFF is the only padding id)");
+    if (hbad & 1u) {
+        set_error("%s: a candidate id is >= n (0xFFFFFFFF is the only padding id)", name);
+        return MIH_EINVAL;
+    }
+    if (hbad & 2u) {
+        set_error("%s: a candidate row is longer than k_in (or its offsets decrease)", name);
+        return MIH_EINVAL;
+    }
+    if (hbad & 4u) {
+        set_error("%s: a result row is longer than MIH_MAX_K (or its offsets decrease)", name);
         return MIH_EINVAL;
     }
     return MIH_OK;
+}
+
+}  // namespace
+}  // namespace mih
+
+extern "C" mih_status mih_rerank_asym(const uint64_t* codes, uint64_t n, int q, const float* proj, uint32_t nq,
+                                      const uint32_t* ids, uint32_t k_in, uint32_t k, uint32_t* out_ids,
+                                      double* out_a, void* stream) {
+    return mih::rerank_call("mih_rerank_asym", codes, n, q, proj, nq, ids, nullptr, k_in, nullptr, k, out_ids,
+                            out_a, stream);
+}
+
+extern "C" mih_status mih_rerank_asym_csr(const uint64_t* codes, uint64_t n, int q, const float* proj,
+                                          uint32_t nq, const uint32_t* ids, const uint64_t* in_offsets,
+                                          uint32_t k_in_max, const uint64_t* out_offsets, uint32_t* out_ids,
+                                          double* out_a, void* stream) {
+    if (in_offsets == nullptr || out_offsets == nullptr) {
+        mih::clear_error();
+        mih::set_error("mih_rerank_asym_csr: in_offsets and out_offsets are required");
+        return MIH_EINVAL;
+    }
+    return mih::rerank_call("mih_rerank_asym_csr", codes, n, q, proj, nq, ids, in_offsets, k_in_max, out_offsets,
+                            0u, out_ids, out_a, stream);
 }

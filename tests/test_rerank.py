@@ -136,3 +136,38 @@ def test_rerank_errors(gpu_lib):
         mih.mih_rerank_asym(codes, 64, proj, ok, 0)
     empty = mih.mih_rerank_asym(codes, 64, proj[:0], ok[:0], 4)
     assert empty["ids"].shape == (0, 4)
+
+
+@pytest.mark.parametrize("kmax", [100, 300])
+def test_rerank_csr_after_per_query_k(gpu_lib, orc, kmax):
+    """Per-query k: mih_knn's CSR answers (k log-uniform in [1, kmax]) re-ranked
+    to ceil(k_i / 2) per row by mih_rerank_asym_csr, against the oracle row by
+    row (kmax 100: rows sorted by one warp; 300: by a CTA)."""
+    import torch
+
+    mih = gpu_lib
+    q, n, nq = 128, 100_000, 200
+    dev = torch.device("cuda", 0)
+    db, _ = synth.lsh_projections(n, q, 80)
+    qc, proj = synth.lsh_projections(nq, q, 81)
+    codes = torch.from_numpy(db.view(np.int64)).to(dev)
+    queries = torch.from_numpy(qc.view(np.int64)).to(dev)
+    kq = synth.per_query_k(nq, seed=5, kmax=kmax)
+    ix = mih.mih_build(codes, q, 4)
+    r = mih.mih_knn(ix, queries, torch.from_numpy(kq.astype(np.int32)).to(dev))
+    ix.free()
+    kout = (kq.astype(np.int64) + 1) // 2
+    ooff = np.concatenate([[0], np.cumsum(kout)]).astype(np.int64)
+    rr = mih.mih_rerank_asym_csr(codes, q, torch.from_numpy(proj).to(dev), r["ids"], r["offsets"],
+                                 torch.from_numpy(ooff).to(dev))
+    got_ids, got_a = rr["ids"].cpu().numpy().view(np.uint32), rr["a"].cpu().numpy()
+    off = r["offsets"].cpu().numpy().astype(np.int64)
+    cand = r["ids"].cpu().numpy().view(np.uint32)
+    for i in range(nq):
+        want_ids, want_a = orc.rerank_asym(db, proj[i:i + 1], cand[off[i]:off[i + 1]][None, :], int(kout[i]))
+        assert np.array_equal(got_ids[ooff[i]:ooff[i + 1]], want_ids[0]), i
+        assert np.array_equal(got_a[ooff[i]:ooff[i + 1]], want_a[0]), i
+    # a row longer than the stated maximum is an error
+    with pytest.raises(mih.MihError):
+        mih.mih_rerank_asym_csr(codes, q, torch.from_numpy(proj).to(dev), r["ids"], r["offsets"],
+                                torch.from_numpy(ooff).to(dev), k_in_max=int(kq.max()) - 1)
