@@ -37,3 +37,21 @@ def test_dram_summary_fields():
     else:
         assert got == (None, None)
     assert bench.slice_traffic({}, 1, {}, 1, int(kv["q"]), kv["codes"], int(kv["n"]) + 1, int(kv["m"])) == (None, None)
+
+
+def test_reference_arm_prints_its_line():
+    """`bench.py --impl reference` (the oracle timed on the host) prints one
+    JSON line with the contract's keys, on a small database."""
+    import json
+    import subprocess
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "20000",
+                          "--steps", "1", "--warmup", "3", "--cpu-sample", "4"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "queries/s" and line["value"] > 0
+    for key in ("metric", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "config"):
+        assert key in line, key
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
